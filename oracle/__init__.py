@@ -1,0 +1,12 @@
+"""CPU oracle for closed-shell Hartree-Fock (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the library under
+``paper_1303_4916_gb300/`` never does, and this package never imports it.
+
+``Basis`` wraps the plain C implementation in ``hf_oracle.c`` (integrals,
+Boys function, J/K); ``rhf`` in ``scf.py`` runs the textbook RHF iteration
+on top of it with numpy.
+"""
+from .core import Basis, boys, build_oracle, oracle_threads  # noqa: F401
+from .scf import rhf, RHFResult, LinearDependence  # noqa: F401

@@ -1,0 +1,141 @@
+"""Textbook closed-shell RHF iteration (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The steps follow the Szabo-Ostlund SCF procedure the paper builds on
+(Sec. "Introduction" and "Capabilities": Hartree-Fock; DIIS of Pulay in
+Sec. "Technical details"):
+
+1. X = S^{-1/2} (symmetric Loewdin orthogonalisation, X = U s^{-1/2} U^T);
+   lambda_min(S) < 1e-10 is rejected as linear dependence.
+2. Core guess: D_0 = 0, so F_0 = H = T + V.
+3. For k = 1 .. max_iter:
+   F' = X^T F_{k-1} X;  F' C' = C' eps (ascending);  C = X C';
+   D_k = C_occ C_occ^T with n_occ = N_e / 2;
+   J, K from D_k (J/K equation with P = D_k);  F_k = H + 2J - K;
+   E_k = Tr[D_k (H + F_k)] + E_nuc;
+   with DIIS on: error e_k = F_k D_k S - S D_k F_k, keep the most recent
+   ``diis_size`` (F, e); once two or more are stored, replace F_k by
+   sum_i c_i F_i with c from the Pulay system [B -1; -1 0][c; lam] = [0; -1],
+   B_ij = <e_i, e_j>; when B is singular (cond > 1e14) the oldest pair is
+   dropped and the system solved again;
+   stop when |E_k - E_{k-1}| <= e_tol.
+
+With P = 2 D this is the same as Szabo-Ostlund's F = H + J[P] - K[P]/2.
+The eigen-decompositions and the small linear solve use numpy's LAPACK
+routines as plain library steps.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from .core import Basis
+
+
+class LinearDependence(ValueError):
+    pass
+
+
+@dataclass
+class RHFResult:
+    energy: float
+    e_elec: float
+    e_nuc: float
+    converged: bool
+    iterations: int
+    D: np.ndarray
+    C: np.ndarray
+    eps: np.ndarray
+    F: np.ndarray          # F_k of the last iteration, before any DIIS extrapolation
+    F1: np.ndarray         # F_1 = F(D_1), D_1 from diagonalising H
+    energies: List[float] = field(default_factory=list)
+    homo_lumo_gap: float = float("nan")
+    diis_error: float = float("nan")
+    H: Optional[np.ndarray] = None
+    S: Optional[np.ndarray] = None
+
+
+def lowdin(S: np.ndarray, min_eig: float = 1e-10) -> np.ndarray:
+    s, U = np.linalg.eigh(S)
+    if s[0] < min_eig:
+        raise LinearDependence(f"lambda_min(S) = {s[0]:.3e} < {min_eig:g}")
+    return (U * (1.0 / np.sqrt(s))) @ U.T
+
+
+def diis_extrapolate(Fs, es):
+    """Pulay DIIS: returns sum_i c_i F_i with sum_i c_i = 1 minimising |sum c_i e_i|."""
+    Fs = list(Fs)
+    es = list(es)
+    while len(Fs) >= 2:
+        m = len(Fs)
+        B = np.empty((m + 1, m + 1))
+        for i in range(m):
+            for j in range(m):
+                B[i, j] = float(np.sum(es[i] * es[j]))
+        B[m, :m] = -1.0
+        B[:m, m] = -1.0
+        B[m, m] = 0.0
+        rhs = np.zeros(m + 1)
+        rhs[m] = -1.0
+        if np.linalg.cond(B) > 1e14:
+            Fs.pop(0)
+            es.pop(0)
+            continue
+        c = np.linalg.solve(B, rhs)[:m]
+        return sum(ci * Fi for ci, Fi in zip(c, Fs))
+    return Fs[-1]
+
+
+def rhf(mol, max_iter: int = 30, e_tol: float = 1e-8, diis_size: int = 0,
+        tau: float = 0.0, nthreads: int = 1, basis: Optional[Basis] = None,
+        D0: Optional[np.ndarray] = None) -> RHFResult:
+    B = basis if basis is not None else Basis(mol)
+    S, T, V = B.one_electron()
+    H = T + V
+    e_nuc = B.nuclear_repulsion()
+    X = lowdin(S)
+    nocc = mol.n_electrons // 2
+    if D0 is None:
+        F = H.copy()
+    else:
+        J, K, _ = B.jk(D0, tau, nthreads)
+        F = H + 2.0 * J - K
+    e_old = None
+    energies = []
+    Fs, es = [], []
+    F1 = None
+    converged = False
+    k = 0
+    for k in range(1, max_iter + 1):
+        Fp = X.T @ F @ X
+        eps, Cp = np.linalg.eigh(Fp)
+        C = X @ Cp
+        Cocc = C[:, :nocc]
+        D = Cocc @ Cocc.T
+        J, K, _ = B.jk(D, tau, nthreads)
+        Fk = H + 2.0 * J - K
+        E = float(np.sum(D * (H + Fk))) + e_nuc
+        energies.append(E)
+        if F1 is None:
+            F1 = Fk.copy()
+        err = Fk @ D @ S - S @ D @ Fk
+        F = Fk
+        if diis_size > 0:
+            Fs.append(Fk)
+            es.append(err)
+            if len(Fs) > diis_size:
+                Fs.pop(0)
+                es.pop(0)
+            if len(Fs) >= 2:
+                F = diis_extrapolate(Fs, es)
+        if e_old is not None and abs(E - e_old) <= e_tol:
+            converged = True
+            break
+        e_old = E
+    gap = float(eps[nocc] - eps[nocc - 1]) if nocc < eps.shape[0] and nocc > 0 else float("nan")
+    return RHFResult(energy=E, e_elec=E - e_nuc, e_nuc=e_nuc, converged=converged,
+                     iterations=k, D=D, C=C, eps=eps, F=Fk, F1=F1, energies=energies,
+                     homo_lumo_gap=gap, diis_error=float(np.abs(err).max()), H=H, S=S)

@@ -1,0 +1,235 @@
+"""Seeded synthetic molecules (geometry, charges, shells, exponents, raw coefficients).
+
+The paper's benchmark systems (atoms and H2O in 3-21G / cc-pVTZ / cc-pVQZ
+basis sets, Fig. 3 and Fig. 4) need basis-library files that are not
+available here, so the workloads are synthetic molecules of the same size
+range built from the rules below.  Every draw comes from
+``numpy.random.default_rng(seed)`` (PCG64) in a fixed order: geometry,
+charges, then for each shell its exponents followed by its coefficients.
+
+Coordinates are in bohr, as in the paper's input file (Sec. "Using the
+code").  Shell angular momentum l is 0, 1 or 2 (Cartesian s, p, d).
+Coefficients are raw draws; normalisation (Eq. 1 basis functions with unit
+self-overlap) is left to the consumer.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List
+
+import numpy as np
+
+
+@dataclass
+class Molecule:
+    """One molecule and its contracted Cartesian Gaussian basis (Eq. 1).
+
+    Arrays:
+      Z            int32  [natom]       nuclear charges
+      xyz          f64    [natom, 3]    nuclear positions (bohr)
+      shell_atom   int32  [nshell]      atom index of each shell centre
+      shell_l      int32  [nshell]      angular momentum l = L+M+N
+      shell_nprim  int32  [nshell]      primitives in the contraction
+      shell_prim   int32  [nshell]      offset of the shell's first primitive
+      exps         f64    [nprim]       primitive exponents alpha
+      coefs        f64    [nprim]       raw contraction coefficients d
+    """
+
+    Z: np.ndarray
+    xyz: np.ndarray
+    shell_atom: np.ndarray
+    shell_l: np.ndarray
+    shell_nprim: np.ndarray
+    shell_prim: np.ndarray
+    exps: np.ndarray
+    coefs: np.ndarray
+    n_electrons: int
+    name: str = ""
+    seed: int = -1
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def natom(self) -> int:
+        return int(self.Z.shape[0])
+
+    @property
+    def nshell(self) -> int:
+        return int(self.shell_l.shape[0])
+
+    @property
+    def nbf(self) -> int:
+        """Number of Cartesian basis functions: (l+1)(l+2)/2 per shell."""
+        l = self.shell_l.astype(np.int64)
+        return int(((l + 1) * (l + 2) // 2).sum())
+
+    def copy(self) -> "Molecule":
+        return Molecule(self.Z.copy(), self.xyz.copy(), self.shell_atom.copy(),
+                        self.shell_l.copy(), self.shell_nprim.copy(),
+                        self.shell_prim.copy(), self.exps.copy(),
+                        self.coefs.copy(), self.n_electrons, self.name,
+                        self.seed, dict(self.meta))
+
+
+def _pack(Z, xyz, shells, name, seed, n_electrons=None) -> Molecule:
+    """shells: list of (atom, l, exps[], coefs[])."""
+    sa, sl, sn, sp, ex, co = [], [], [], [], [], []
+    off = 0
+    for atom, l, e, c in shells:
+        sa.append(atom)
+        sl.append(l)
+        sn.append(len(e))
+        sp.append(off)
+        ex.extend(float(v) for v in e)
+        co.extend(float(v) for v in c)
+        off += len(e)
+    Z = np.asarray(Z, dtype=np.int32)
+    if n_electrons is None:
+        n_electrons = int(Z.sum())
+        if n_electrons % 2:
+            # Closed-shell RHF needs an even count: an odd total is read as
+            # the singly charged cation.
+            n_electrons -= 1
+    return Molecule(Z=Z, xyz=np.asarray(xyz, dtype=np.float64).reshape(-1, 3),
+                    shell_atom=np.asarray(sa, dtype=np.int32),
+                    shell_l=np.asarray(sl, dtype=np.int32),
+                    shell_nprim=np.asarray(sn, dtype=np.int32),
+                    shell_prim=np.asarray(sp, dtype=np.int32),
+                    exps=np.asarray(ex, dtype=np.float64),
+                    coefs=np.asarray(co, dtype=np.float64),
+                    n_electrons=int(n_electrons), name=name, seed=seed)
+
+
+def _log_uniform(rng, lo, hi, n):
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n))
+
+
+def h_line(n_atoms: int = 8, seed: int = 0, spacing: float = 1.4,
+           jitter: float = 0.1, nprim: int = 3,
+           exp_range=(0.1, 10.0), coef_range=(0.2, 1.0)) -> Molecule:
+    """Hydrogen chain on a jittered line, one contracted s shell per atom.
+
+    x_i = spacing*i + U(-jitter, jitter); y, z = U(-jitter, jitter).
+    Defaults: 8 atoms, 1.4 bohr, 3 primitives with exponents log-uniform in
+    [0.1, 10] and coefficients uniform in [0.2, 1]; 8 electrons.
+    """
+    rng = np.random.default_rng(seed)
+    xyz = np.zeros((n_atoms, 3))
+    for i in range(n_atoms):
+        d = rng.uniform(-jitter, jitter, size=3)
+        xyz[i] = (spacing * i + d[0], d[1], d[2])
+    Z = np.ones(n_atoms, dtype=np.int32)
+    shells = []
+    for a in range(n_atoms):
+        e = _log_uniform(rng, *exp_range, nprim)
+        c = rng.uniform(*coef_range, size=nprim)
+        shells.append((a, 0, e, c))
+    return _pack(Z, xyz, shells, f"h_line{n_atoms}_s{seed}", seed)
+
+
+# Basis rules.  "sp": hydrogen 2 s shells, C/O 3 s + 2 p, 3 primitives each,
+# exponents log-uniform in [0.05, 50].  "spd": as "sp" plus one Cartesian d
+# shell on C/O, 1..6 primitives per shell, exponents log-uniform [0.03, 200].
+BASIS_RULES = {
+    "sp": dict(h=[0, 0], heavy=[0, 0, 0, 1, 1], nprim=(3, 3), exp=(0.05, 50.0)),
+    "spd": dict(h=[0, 0], heavy=[0, 0, 0, 1, 1, 2], nprim=(1, 6), exp=(0.03, 200.0)),
+    "s": dict(h=[0], heavy=[0, 0], nprim=(3, 3), exp=(0.1, 10.0)),
+}
+
+
+def lattice_molecule(n_atoms: int, seed: int, rules: str = "sp",
+                     spacing: float = 2.4, jitter: float = 0.3,
+                     charges=(1, 6, 8), charge_p=(0.5, 0.3, 0.2),
+                     coef_range=(0.2, 1.0)) -> Molecule:
+    """Atoms on a jittered simple-cubic lattice with a random s/p(/d) basis.
+
+    Sites: the smallest n with n**3 >= n_atoms; the first n_atoms sites in
+    lexicographic (i, j, k) order; each coordinate = spacing*index +
+    U(-jitter, jitter).  Charges drawn from ``charges`` with ``charge_p``.
+    """
+    rr = BASIS_RULES[rules]
+    rng = np.random.default_rng(seed)
+    n = 1
+    while n ** 3 < n_atoms:
+        n += 1
+    sites = [(i, j, k) for i in range(n) for j in range(n) for k in range(n)][:n_atoms]
+    xyz = np.zeros((n_atoms, 3))
+    for a, s in enumerate(sites):
+        xyz[a] = spacing * np.asarray(s, dtype=np.float64) + rng.uniform(-jitter, jitter, size=3)
+    Z = rng.choice(np.asarray(charges), size=n_atoms, p=np.asarray(charge_p)).astype(np.int32)
+    shells = []
+    for a in range(n_atoms):
+        ls = rr["h"] if Z[a] == 1 else rr["heavy"]
+        for l in ls:
+            k = int(rng.integers(rr["nprim"][0], rr["nprim"][1] + 1))
+            e = _log_uniform(rng, *rr["exp"], k)
+            c = rng.uniform(*coef_range, size=k)
+            shells.append((a, l, e, c))
+    m = _pack(Z, xyz, shells, f"lattice{n_atoms}_{rules}_s{seed}", seed)
+    m.meta["rules"] = rules
+    return m
+
+
+def random_shells_molecule(ls, seed: int, nprim=(1, 3), exp_range=(0.2, 3.0),
+                           box: float = 1.5, coef_range=(0.2, 1.0),
+                           Z=None) -> Molecule:
+    """A tiny molecule with one atom per shell of angular momenta ``ls``.
+
+    Used for unit tests on single shell quartets: centres uniform in a cube
+    of side ``box`` bohr, exponents log-uniform in ``exp_range``.
+    """
+    rng = np.random.default_rng(seed)
+    na = len(ls)
+    xyz = rng.uniform(-box / 2, box / 2, size=(na, 3))
+    if Z is None:
+        Z = np.ones(na, dtype=np.int32)
+    shells = []
+    for a, l in enumerate(ls):
+        k = int(rng.integers(nprim[0], nprim[1] + 1))
+        e = _log_uniform(rng, *exp_range, k)
+        c = rng.uniform(*coef_range, size=k)
+        shells.append((a, int(l), e, c))
+    ne = int(np.sum(Z))
+    ne -= ne % 2
+    return _pack(Z, xyz, shells, f"shells{''.join(map(str, ls))}_s{seed}", seed,
+                 n_electrons=ne)
+
+
+def batch_molecules(count: int = 512, seed_base: int = 1000, atoms=(4, 60),
+                    rules: str = "sp", size_seed: int = 999) -> List[Molecule]:
+    """Independent molecules for batched SCF: atom counts uniform in ``atoms``.
+
+    Molecule i uses seed ``seed_base + i``; the atom counts come from their
+    own stream seeded with ``size_seed``.
+    """
+    rng = np.random.default_rng(size_seed)
+    sizes = rng.integers(atoms[0], atoms[1] + 1, size=count)
+    return [lattice_molecule(int(n), seed_base + i, rules) for i, n in enumerate(sizes)]
+
+
+def serve_stream(n_requests: int = 20000, rate: float = 200.0, seed: int = 7,
+                 mol_seed_base: int = 10000, atoms=(4, 150), rules: str = "spd"):
+    """Poisson arrival stream: returns (arrival_times_s, atom_counts, seeds).
+
+    Inter-arrival times are exponential with mean 1/rate; atom counts are
+    log-uniform in ``atoms`` (rounded); molecule i is
+    ``lattice_molecule(atom_counts[i], seeds[i], rules)``.
+    """
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n_requests)
+    t = np.cumsum(gaps)
+    sizes = np.rint(np.exp(rng.uniform(np.log(atoms[0]), np.log(atoms[1]), size=n_requests)))
+    seeds = mol_seed_base + np.arange(n_requests)
+    return t, sizes.astype(np.int64), seeds.astype(np.int64)
+
+
+def concat_basis(mols: List[Molecule]):
+    """Offsets of each molecule inside a packed batch (shells, prims, atoms, bf)."""
+    out = []
+    so = po = ao = bo = 0
+    for m in mols:
+        out.append(dict(shell=so, prim=po, atom=ao, bf=bo))
+        so += m.nshell
+        po += int(m.exps.shape[0])
+        ao += m.natom
+        bo += m.nbf
+    return out

@@ -1,0 +1,313 @@
+"""Pins of the CPU oracle against things other than itself.
+
+* Boys function: F_m(0), the erf closed form of F_0, the large-T asymptote,
+  the downward recursion and direct Gauss-Legendre quadrature.
+* The Szabo-Ostlund H2 / STO-3G worked example (printed to 4 decimals).
+* The closed-form (ss|ss) integral with F_0(T) = sqrt(pi/T) erf(sqrt T) / 2.
+* The single-Gaussian He atom, E(a) = 3a - 8 sqrt(2a/pi) + 2 sqrt(a/pi).
+* Brute-force quadrature (tests/quadrature.py) of S, T, V and ERIs over
+  s, p and d shells, which uses no Boys function and no recurrence.
+* Invariants: 8-fold symmetry, Schwarz inequality, positive semidefinite
+  ERI supermatrix, symmetric J/K, rotation / translation / permutation
+  invariance of the energy, idempotency at convergence.
+* J/K from the unique-quartet digestion against the plain contraction of
+  the full tensor (a different code path in the oracle).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import h_line, lattice_molecule, random_shells_molecule
+from synth.molecules import _pack
+from quadrature import QuadBasis
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Boys
+
+@pytest.mark.parametrize("m", range(0, 13))
+def test_boys_at_zero(m):
+    assert oracle.boys(m, 0.0) == pytest.approx(1.0 / (2 * m + 1), rel=1e-15)
+
+
+@pytest.mark.parametrize("T", [1e-8, 1e-3, 0.1, 0.7, 2.0, 5.5, 11.0, 17.3, 29.99, 30.0, 30.01, 45.0, 120.0])
+def test_boys_f0_erf_closed_form(T):
+    ref = 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))
+    assert oracle.boys(0, T) == pytest.approx(ref, rel=2e-15, abs=1e-300)
+
+
+@pytest.mark.parametrize("m", [0, 1, 3, 6, 8, 12])
+@pytest.mark.parametrize("T", [60.0, 100.0, 400.0])
+def test_boys_large_T_asymptote(m, T):
+    # F_m(T) ~ (2m-1)!! / 2^{m+1} sqrt(pi / T^{2m+1}) up to O(e^{-T}).
+    df = 1.0
+    for k in range(2 * m - 1, 0, -2):
+        df *= k
+    ref = df / 2 ** (m + 1) * math.sqrt(math.pi / T ** (2 * m + 1))
+    assert oracle.boys(m, T) == pytest.approx(ref, rel=1e-14)
+
+
+@pytest.mark.parametrize("T", [0.05, 1.0, 7.0, 20.0, 29.0, 31.0, 50.0])
+def test_boys_downward_recursion(T):
+    # F_m = (2T F_{m+1} + e^{-T}) / (2m+1)
+    for m in range(0, 12):
+        lhs = oracle.boys(m, T)
+        rhs = (2 * T * oracle.boys(m + 1, T) + math.exp(-T)) / (2 * m + 1)
+        assert lhs == pytest.approx(rhs, rel=5e-15)
+
+
+@pytest.mark.parametrize("m", [0, 2, 5, 9])
+@pytest.mark.parametrize("T", [0.0, 0.3, 4.0, 15.0, 33.0])
+def test_boys_gauss_legendre(m, T):
+    x, w = np.polynomial.legendre.leggauss(300)
+    t = 0.5 * (x + 1.0)
+    ref = 0.5 * np.sum(w * t ** (2 * m) * np.exp(-T * t * t))
+    assert oracle.boys(m, T) == pytest.approx(ref, rel=1e-13)
+
+
+# ---------------------------------------------------------------- Szabo-Ostlund H2
+
+def _h2(z2=1):
+    g = json.load(open(os.path.join(GOLDEN, "h2_sto3g.json")))
+    a, d = g["exponents"], g["coefficients"]
+    m = _pack([1, z2], [[0, 0, 0], [g["R_bohr"], 0, 0]], [(0, 0, a, d), (1, 0, a, d)], "h2", 0,
+              n_electrons=2)
+    return m, g
+
+
+def test_szabo_ostlund_h2_sto3g():
+    m, g = _h2()
+    pr, tol = g["printed"], g["tolerance"]
+    B = oracle.Basis(m)
+    S, T, V = B.one_electron()
+    assert S[0, 1] == pytest.approx(pr["S12"], abs=tol)
+    assert T[0, 0] == pytest.approx(pr["T11"], abs=tol)
+    assert T[0, 1] == pytest.approx(pr["T12"], abs=tol)
+    H = T + V
+    assert H[0, 0] == pytest.approx(pr["H11"], abs=tol)
+    assert H[0, 1] == pytest.approx(pr["H12"], abs=tol)
+    # nucleus-1 attraction alone: give atom 2 zero charge
+    m1, _ = _h2(z2=0)
+    _, _, V1 = oracle.Basis(m1).one_electron()
+    assert V1[0, 0] == pytest.approx(pr["V1_11"], abs=tol)
+    assert V1[0, 1] == pytest.approx(pr["V1_12"], abs=tol)
+    assert V1[1, 1] == pytest.approx(pr["V1_22"], abs=tol)
+    assert B.eri(0, 0, 0, 0) == pytest.approx(pr["eri_11_11"], abs=tol)
+    assert B.eri(0, 0, 1, 1) == pytest.approx(pr["eri_11_22"], abs=tol)
+    assert B.eri(1, 0, 0, 0) == pytest.approx(pr["eri_21_11"], abs=tol)
+    assert B.eri(1, 0, 1, 0) == pytest.approx(pr["eri_21_21"], abs=tol)
+    r = oracle.rhf(m, max_iter=50, e_tol=1e-12)
+    assert r.converged
+    assert r.eps[0] == pytest.approx(pr["eps1"], abs=tol)
+    assert r.eps[1] == pytest.approx(pr["eps2"], abs=tol)
+    assert r.e_elec == pytest.approx(pr["E_elec"], abs=tol)
+    assert r.energy == pytest.approx(pr["E_tot"], abs=tol)
+
+
+# ---------------------------------------------------------------- closed forms
+
+def _norm_s(a):
+    return (2.0 * a / math.pi) ** 0.75
+
+
+def _closed_ssss(mol, i, j, k, l):
+    """Contracted (ss|ss) from the closed form, normalised independently."""
+    def shell(s):
+        p0, K = mol.shell_prim[s], mol.shell_nprim[s]
+        e = mol.exps[p0:p0 + K]
+        c = mol.coefs[p0:p0 + K] * np.array([_norm_s(x) for x in e])
+        n2 = sum(c[u] * c[v] * (math.pi / (e[u] + e[v])) ** 1.5 for u in range(K) for v in range(K))
+        return e, c / math.sqrt(n2), mol.xyz[mol.shell_atom[s]]
+    (ea, ca, A), (eb, cb, B), (ec, cc, C), (ed, cd, D) = [shell(s) for s in (i, j, k, l)]
+    tot = 0.0
+    for a, wa in zip(ea, ca):
+        for b, wb in zip(eb, cb):
+            p = a + b
+            P = (a * A + b * B) / p
+            kab = math.exp(-a * b / p * np.sum((A - B) ** 2))
+            for c, wc in zip(ec, cc):
+                for d, wd in zip(ed, cd):
+                    q = c + d
+                    Q = (c * C + d * D) / q
+                    kcd = math.exp(-c * d / q * np.sum((C - D) ** 2))
+                    T = p * q / (p + q) * np.sum((P - Q) ** 2)
+                    f0 = 1.0 if T < 1e-15 else 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))
+                    tot += wa * wb * wc * wd * 2 * math.pi ** 2.5 / (p * q * math.sqrt(p + q)) * kab * kcd * f0
+    return tot
+
+
+def test_ssss_closed_form_h_line():
+    mol = h_line()
+    B = oracle.Basis(mol)
+    rng = np.random.default_rng(5)
+    for _ in range(40):
+        i, j, k, l = rng.integers(0, mol.nshell, size=4)
+        assert B.eri(i, j, k, l) == pytest.approx(_closed_ssss(mol, i, j, k, l), rel=1e-13, abs=1e-15)
+
+
+@pytest.mark.parametrize("alpha", [0.3, 0.7671, 2.5])
+def test_single_gaussian_helium(alpha):
+    m = _pack([2], [[0.1, -0.2, 0.3]], [(0, 0, [alpha], [1.0])], "he", 0, n_electrons=2)
+    r = oracle.rhf(m, max_iter=5, e_tol=1e-13)
+    ref = 3 * alpha - 8 * math.sqrt(2 * alpha / math.pi) + 2 * math.sqrt(alpha / math.pi)
+    assert r.energy == pytest.approx(ref, rel=1e-13)
+    # minimum over alpha: E = -(8 sqrt 2 - 2)^2 / (12 pi) ~ -2.3010
+    if alpha == 0.7671:
+        assert r.energy == pytest.approx(-(8 * math.sqrt(2) - 2) ** 2 / (12 * math.pi), abs=2e-6)
+
+
+# ---------------------------------------------------------------- quadrature
+
+@pytest.mark.parametrize("ls,seed", [((0, 1, 2), 3), ((2, 2, 1), 11), ((1, 0), 4)])
+def test_one_electron_vs_quadrature(ls, seed):
+    mol = random_shells_molecule(ls, seed, nprim=(1, 2), Z=np.array([1, 3, 2][:len(ls)], dtype=np.int32))
+    B = oracle.Basis(mol)
+    S, T, V = B.one_electron()
+    Q = QuadBasis(mol)
+    n = B.nbf
+    for i in range(n):
+        assert S[i, i] == pytest.approx(1.0, abs=1e-13)
+        for j in range(n):
+            assert S[i, j] == pytest.approx(Q.overlap(i, j), abs=1e-12)
+            assert T[i, j] == pytest.approx(Q.kinetic(i, j), abs=1e-11)
+    rng = np.random.default_rng(seed)
+    for _ in range(12):
+        i, j = rng.integers(0, n, size=2)
+        assert V[i, j] == pytest.approx(Q.nuclear(i, j), abs=1e-10)
+
+
+@pytest.mark.parametrize("ls,seed", [((1, 0, 1, 0), 1), ((1, 1, 1, 1), 2), ((2, 0, 1, 0), 3),
+                                     ((2, 1, 2, 0), 4), ((2, 2, 2, 2), 5), ((0, 0, 0, 0), 6)])
+def test_eri_vs_quadrature(ls, seed):
+    mol = random_shells_molecule(ls, seed, nprim=(1, 2), exp_range=(0.3, 2.5))
+    B = oracle.Basis(mol)
+    Q = QuadBasis(mol)
+    sb = B.shell_bf
+    blk = B.eri_shell_block(0, 1, 2, 3)
+    rng = np.random.default_rng(seed)
+    idx = [tuple(rng.integers(0, blk.shape[x]) for x in range(4)) for _ in range(10)]
+    for (a, b, c, d) in idx:
+        ref = Q.eri(sb[0] + a, sb[1] + b, sb[2] + c, sb[3] + d)
+        assert blk[a, b, c, d] == pytest.approx(ref, rel=1e-9, abs=1e-12)
+
+
+# ---------------------------------------------------------------- invariants
+
+def _small_spd(seed=7):
+    return random_shells_molecule((2, 1, 0, 1, 2), seed, nprim=(1, 2), exp_range=(0.2, 3.0), box=3.0,
+                                  Z=np.array([6, 1, 1, 8, 1], dtype=np.int32))
+
+
+def test_eri_tensor_symmetry_schwarz_psd():
+    mol = _small_spd()
+    B = oracle.Basis(mol)
+    G = B.eri_tensor()
+    for perm in [(1, 0, 2, 3), (0, 1, 3, 2), (2, 3, 0, 1), (3, 2, 1, 0)]:
+        np.testing.assert_allclose(G, G.transpose(perm), atol=1e-13, rtol=0)
+    n = B.nbf
+    diag = np.einsum("ijij->ij", G)
+    bound = np.sqrt(np.einsum("ij,kl->ijkl", diag, diag))
+    assert np.all(np.abs(G) <= bound * (1 + 1e-12) + 1e-14)
+    M = G.reshape(n * n, n * n)
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > -1e-12
+    Q = B.schwarz()
+    sb = B.shell_bf
+    for a in range(mol.nshell):
+        for b in range(mol.nshell):
+            blk = diag[sb[a]:sb[a + 1], sb[b]:sb[b + 1]]
+            assert Q[a, b] == pytest.approx(math.sqrt(np.abs(blk).max()), rel=1e-14)
+
+
+def _rand_density(n, seed, nocc=None):
+    rng = np.random.default_rng(seed)
+    C = rng.normal(size=(n, nocc or max(1, n // 3))) / math.sqrt(n)
+    return C @ C.T
+
+
+def test_jk_digest_matches_full_contraction():
+    mol = _small_spd()
+    B = oracle.Basis(mol)
+    G = B.eri_tensor()
+    D = _rand_density(B.nbf, 3)
+    J, K, nq = B.jk(D)
+    np.testing.assert_allclose(J, np.einsum("ijkl,kl->ij", G, D), atol=1e-12, rtol=0)
+    np.testing.assert_allclose(K, np.einsum("ijkl,jk->il", G, D), atol=1e-12, rtol=0)
+    ns = mol.nshell
+    npair = ns * (ns + 1) // 2
+    assert nq == npair * (npair + 1) // 2
+    np.testing.assert_allclose(J, J.T, atol=1e-13)
+    np.testing.assert_allclose(K, K.T, atol=1e-13)
+    assert np.sum(D * J) >= 0 and np.sum(D * K) >= 0
+    rows = np.array([0, 4, B.nbf - 1])
+    Jr, Kr = B.jk_rows(D, rows)
+    np.testing.assert_allclose(Jr, J[rows], atol=1e-12, rtol=0)
+    np.testing.assert_allclose(Kr, K[rows], atol=1e-12, rtol=0)
+    J2, K2, _ = B.jk(D, nthreads=3)
+    np.testing.assert_allclose(J2, J, atol=1e-13)
+    np.testing.assert_allclose(K2, K, atol=1e-13)
+
+
+def test_schwarz_screening_is_bounded():
+    mol = lattice_molecule(6, 3, "sp")
+    B = oracle.Basis(mol)
+    D = _rand_density(B.nbf, 4)
+    J0, K0, n0 = B.jk(D)
+    tau = 1e-6
+    J1, K1, n1 = B.jk(D, tau=tau)
+    assert n1 < n0
+    assert n1 == B.count_quartets(tau)
+    # each dropped integral is below tau in magnitude; each is used in at most
+    # 8 places of J and K with |D| entries
+    dropped = n0 - n1
+    bound = 8 * dropped * 36 * tau * np.abs(D).max()
+    assert np.abs(J1 - J0).max() <= bound
+    assert np.abs(K1 - K0).max() <= bound
+
+
+def _rotation(seed):
+    rng = np.random.default_rng(seed)
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] *= -1
+    return q
+
+
+def test_energy_invariances():
+    mol = random_shells_molecule((1, 0, 2, 1), 21, nprim=(1, 2), exp_range=(0.3, 3.0), box=3.5,
+                                 Z=np.array([3, 1, 2, 2], dtype=np.int32))
+    e0 = oracle.rhf(mol, max_iter=80, e_tol=1e-11, diis_size=6)
+    assert e0.converged
+    R = _rotation(1)
+    m2 = mol.copy()
+    m2.xyz = mol.xyz @ R.T + np.array([0.3, -1.2, 2.0])
+    e1 = oracle.rhf(m2, max_iter=80, e_tol=1e-11, diis_size=6)
+    assert e1.energy == pytest.approx(e0.energy, abs=1e-9)
+    # permute atoms (shells follow their atoms)
+    perm = np.array([2, 0, 3, 1])
+    inv = np.argsort(perm)
+    m3 = mol.copy()
+    m3.Z = mol.Z[perm]
+    m3.xyz = mol.xyz[perm]
+    m3.shell_atom = inv[mol.shell_atom].astype(np.int32)
+    e2 = oracle.rhf(m3, max_iter=80, e_tol=1e-11, diis_size=6)
+    assert e2.energy == pytest.approx(e0.energy, abs=1e-9)
+    # stationarity and idempotency at convergence
+    D, S, F = e0.D, e0.S, e0.F
+    np.testing.assert_allclose(D @ S @ D, D, atol=1e-6)
+    assert np.trace(D @ S) == pytest.approx(mol.n_electrons // 2, abs=1e-9)
+    assert np.abs(F @ D @ S - S @ D @ F).max() < 1e-4
+
+
+def test_scf_h_line_no_diis():
+    mol = h_line()
+    r = oracle.rhf(mol, max_iter=30, e_tol=1e-8, diis_size=0)
+    assert r.converged
+    assert r.energy < 0
+    # variational: the SCF energy is not above the core-guess energy of D_1
+    assert r.energy <= r.energies[0] + 1e-12
