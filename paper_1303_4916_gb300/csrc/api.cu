@@ -1,0 +1,200 @@
+// api.cu -- context, error reporting, device allocation, Boys tables.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hf_internal.h"
+
+static thread_local std::string g_last_error;
+
+int hf_fail(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+extern "C" const char* hf_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* hf_strerror(int code) {
+  switch (code) {
+    case HF_OK: return "ok";
+    case HF_PENDING: return "pending";
+    case HF_ERR_INVALID: return "invalid argument";
+    case HF_ERR_UNSUPPORTED_L: return "unsupported angular momentum";
+    case HF_ERR_OOM: return "out of memory";
+    case HF_ERR_LINDEP: return "linearly dependent basis";
+    case HF_ERR_NOT_CONVERGED: return "SCF not converged";
+    case HF_ERR_TIMEOUT: return "timeout";
+    case HF_ERR_CUDA: return "CUDA error";
+    case HF_ERR_ODD_ELECTRONS: return "odd electron count";
+    case HF_ERR_NOT_FOUND: return "not found";
+    case HF_ERR_QUEUE_FULL: return "queue full";
+    case HF_ERR_CANCELLED: return "cancelled";
+    case HF_ERR_TOO_LARGE: return "request exceeds memory budget";
+    default: return "unknown error";
+  }
+}
+
+extern "C" void hf_jk_opts_default(hf_jk_opts* o) {
+  if (!o) return;
+  o->schwarz_tau = 1e-12;
+  o->fp32_bound = 0.0;
+  o->flags = 0;
+}
+
+extern "C" void hf_scf_opts_default(hf_scf_opts* o) {
+  if (!o) return;
+  o->max_iter = 128;
+  o->e_tol = 1e-8;
+  o->diis_size = 8;
+  o->D0 = nullptr;
+  hf_jk_opts_default(&o->jk);
+  o->flags = 0;
+}
+
+int hf_dev_alloc(hf_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return HF_OK;
+  int c = ctx->fail_countdown.load();
+  if (c > 0) {
+    if (ctx->fail_countdown.fetch_sub(1) == 1)
+      return hf_fail(HF_ERR_OOM, "injected allocation failure (%zu bytes)", bytes);
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return hf_fail(HF_ERR_OOM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->device_bytes += (long long)bytes;
+  return HF_OK;
+}
+
+void hf_dev_free(hf_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFreeAsync(p, ctx->stream);
+  ctx->device_bytes -= (long long)bytes;
+}
+
+// ------------------------------------------------------------- Boys table
+// Row i: F_m(T_i), m = 0..BOYS_NM-1, and exp(-T_i), T_i = i*BOYS_H, in long
+// double: F_{NM-1}(T) from its power series
+//   F_m(T) = exp(-T) sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)),
+// the lower orders by the downward recursion F_m = (2T F_{m+1} + e^{-T})/(2m+1),
+// which is stable in that direction.
+static void boys_row(long double T, long double* out) {
+  const int M = BOYS_NM - 1;
+  long double term = 1.0L / (2 * M + 1), sum = term;
+  for (int k = 1; k < 5000; ++k) {
+    term *= 2.0L * T / (long double)(2 * M + 2 * k + 1);
+    sum += term;
+    if (term <= sum * 1e-21L) break;
+  }
+  const long double et = expl(-T);
+  out[M] = et * sum;
+  for (int m = M - 1; m >= 0; --m) out[m] = (2.0L * T * out[m + 1] + et) / (long double)(2 * m + 1);
+  out[BOYS_NM] = et;
+}
+
+int hf_boys_tables(hf_ctx* ctx) {
+  std::vector<double> t64((size_t)BOYS_NGRID * BOYS_STRIDE);
+  std::vector<float> t32((size_t)BOYS_NGRID * BOYS_STRIDE);
+  long double row[BOYS_STRIDE];
+  for (int i = 0; i < BOYS_NGRID; ++i) {
+    boys_row((long double)i * (long double)BOYS_H, row);
+    for (int k = 0; k < BOYS_STRIDE; ++k) {
+      t64[(size_t)i * BOYS_STRIDE + k] = (double)row[k];
+      t32[(size_t)i * BOYS_STRIDE + k] = (float)row[k];
+    }
+  }
+  void* p = nullptr;
+  HF_CHECK(hf_dev_alloc(ctx, &p, t64.size() * sizeof(double)));
+  ctx->boys64 = (double*)p;
+  HF_CHECK(hf_dev_alloc(ctx, &p, t32.size() * sizeof(float)));
+  ctx->boys32 = (float*)p;
+  HF_CUDA(cudaMemcpyAsync(ctx->boys64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  HF_CUDA(cudaMemcpyAsync(ctx->boys32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  HF_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HF_OK;
+}
+
+// ------------------------------------------------------------- context
+extern "C" int hf_ctx_create(hf_ctx** out, int device, size_t hbm_budget, void* cuda_stream) {
+  if (!out) return hf_fail(HF_ERR_INVALID, "hf_ctx_create: out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return hf_fail(HF_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= ndev) return hf_fail(HF_ERR_INVALID, "device %d out of range (%d)", device, ndev);
+  hf_ctx* c = new (std::nothrow) hf_ctx();
+  if (!c) return hf_fail(HF_ERR_OOM, "host allocation");
+  c->device = device;
+  int rc = HF_OK;
+  do {
+    if (cudaSetDevice(device) != cudaSuccess) { rc = hf_fail(HF_ERR_CUDA, "cudaSetDevice"); break; }
+    if (cuda_stream) {
+      c->stream = (cudaStream_t)cuda_stream;
+    } else {
+      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        rc = hf_fail(HF_ERR_CUDA, "cudaStreamCreate");
+        break;
+      }
+      c->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    c->hbm_budget = hbm_budget ? hbm_budget : (size_t)(0.8 * (double)fr);
+    if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) { rc = hf_fail(HF_ERR_CUDA, "cublasCreate"); break; }
+    cublasSetStream(c->cublas, c->stream);
+    if (cusolverDnCreate(&c->cusolver) != CUSOLVER_STATUS_SUCCESS) {
+      rc = hf_fail(HF_ERR_CUDA, "cusolverDnCreate");
+      break;
+    }
+    cusolverDnSetStream(c->cusolver, c->stream);
+    hf_register_classes_sp(c->ops);
+    hf_register_classes_d1(c->ops);
+    hf_register_classes_d2(c->ops);
+    hf_register_classes_d3(c->ops);
+    hf_register_classes_d4(c->ops);
+    hf_register_classes_d5(c->ops);
+    hf_register_classes_d6(c->ops);
+    for (int k = 0; k < HF_NCLASS; ++k)
+      if (!c->ops[k].jk64) { rc = hf_fail(HF_ERR_CUDA, "class %d has no kernels", k); break; }
+    if (rc != HF_OK) break;
+    rc = hf_boys_tables(c);
+  } while (0);
+  if (rc != HF_OK) {
+    hf_ctx_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return HF_OK;
+}
+
+extern "C" void hf_ctx_destroy(hf_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->boys64) hf_dev_free(c, c->boys64, 0);
+  if (c->boys32) hf_dev_free(c, c->boys32, 0);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->cublas) cublasDestroy(c->cublas);
+  if (c->cusolver) cusolverDnDestroy(c->cusolver);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+extern "C" void* hf_ctx_stream(hf_ctx* c) { return c ? (void*)c->stream : nullptr; }
+extern "C" int hf_ctx_num_sms(hf_ctx* c) { return c ? c->num_sms : 0; }
+extern "C" void hf_ctx_inject_alloc_failure(hf_ctx* c, int n) {
+  if (c) c->fail_countdown.store(n > 0 ? n : 0);
+}

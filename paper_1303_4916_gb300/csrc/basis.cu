@@ -1,0 +1,689 @@
+// basis.cu -- basis construction, shell-pair data, Schwarz factors,
+// quartet bucketing, the J/K launch sequence, one-electron integrals and the
+// stored-tensor path.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "eri.cuh"
+#include "hf_internal.h"
+
+#define HF_MAX_NPRIM 16
+static const double kPi = 3.14159265358979323846;
+
+// Primitive pairs whose magnitude bound is below this are skipped; their
+// contribution to any integral is below ~1e-16.
+static const double kPrimEps = 1e-17;
+
+static double dfact(int n) {
+  double r = 1.0;
+  for (int k = n; k > 1; k -= 2) r *= k;
+  return r;
+}
+
+static int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+// ------------------------------------------------------------- pair kernel
+// One thread per shell pair (A, B), l_A >= l_B: for each primitive pair
+// p = a + b, P = (a A + b B)/p, PA = P - A and
+// K = c_a c_b exp(-ab/p |AB|^2) sqrt(2) pi^(5/4) / p; records are sorted by
+// the magnitude bound |K| (2p)^(-1/4) (1 + |AB| + p^(-1/2))^(l_A+l_B) and
+// those below kPrimEps are not counted.
+__global__ void pair_kernel(int npairs, const int* __restrict__ pA, const int* __restrict__ pB,
+                            const int* __restrict__ poff, const double* __restrict__ sh_xyz,
+                            const int* __restrict__ sh_l, const int* __restrict__ sh_nprim,
+                            const int* __restrict__ sh_prim, const int* __restrict__ sh_bf,
+                            const double* __restrict__ exps, const double* __restrict__ coefs,
+                            double* __restrict__ prim64, float* __restrict__ prim32, PairInfo* __restrict__ info,
+                            double eps) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npairs) return;
+  const int A = pA[t], B = pB[t];
+  const double Ax = sh_xyz[3 * A], Ay = sh_xyz[3 * A + 1], Az = sh_xyz[3 * A + 2];
+  const double Bx = sh_xyz[3 * B], By = sh_xyz[3 * B + 1], Bz = sh_xyz[3 * B + 2];
+  const double ABx = Ax - Bx, ABy = Ay - By, ABz = Az - Bz;
+  const double r2 = ABx * ABx + ABy * ABy + ABz * ABz;
+  const double rab = sqrt(r2);
+  const int KA = sh_nprim[A], KB = sh_nprim[B], l = sh_l[A] + sh_l[B];
+  const int n = KA * KB;
+  double mag[HF_MAX_NPRIM * HF_MAX_NPRIM];
+  int order[HF_MAX_NPRIM * HF_MAX_NPRIM];
+  for (int k = 0; k < n; ++k) {
+    const double a = exps[sh_prim[A] + k / KB], b = exps[sh_prim[B] + k % KB];
+    const double p = a + b;
+    const double K = coefs[sh_prim[A] + k / KB] * coefs[sh_prim[B] + k % KB] * exp(-a * b / p * r2) * 1.4142135623730951 *
+                     pow(kPi, 1.25) / p;
+    mag[k] = fabs(K) * pow(2.0 * p, -0.25) * pow(1.0 + rab + 1.0 / sqrt(p), (double)l);
+    order[k] = k;
+  }
+  for (int i = 1; i < n; ++i) {  // insertion sort, descending magnitude
+    const int o = order[i];
+    int j = i - 1;
+    while (j >= 0 && mag[order[j]] < mag[o]) {
+      order[j + 1] = order[j];
+      --j;
+    }
+    order[j + 1] = o;
+  }
+  int nsig = 0;
+  const int base = poff[t];
+  for (int s = 0; s < n; ++s) {
+    const int k = order[s];
+    if (mag[k] >= eps) ++nsig;
+    const double a = exps[sh_prim[A] + k / KB], b = exps[sh_prim[B] + k % KB];
+    const double p = a + b;
+    const double K = coefs[sh_prim[A] + k / KB] * coefs[sh_prim[B] + k % KB] * exp(-a * b / p * r2) * 1.4142135623730951 *
+                     pow(kPi, 1.25) / p;
+    const double Px = (a * Ax + b * Bx) / p, Py = (a * Ay + b * By) / p, Pz = (a * Az + b * Bz) / p;
+    double* r = prim64 + (size_t)(base + s) * PRIM64_STRIDE;
+    r[0] = p; r[1] = 0.5 / p; r[2] = Px; r[3] = Py; r[4] = Pz;
+    r[5] = Px - Ax; r[6] = Py - Ay; r[7] = Pz - Az; r[8] = K; r[9] = 0.0;
+    float* f = prim32 + (size_t)(base + s) * PRIM32_STRIDE;
+    for (int x = 0; x < 10; ++x) f[x] = (float)r[x];
+    f[10] = 0.f; f[11] = 0.f;
+  }
+  PairInfo pi;
+  pi.bfA = sh_bf[A];
+  pi.bfB = sh_bf[B];
+  pi.prim0 = base;
+  pi.nprim = nsig;
+  pi.AB[0] = ABx; pi.AB[1] = ABy; pi.AB[2] = ABz;
+  pi.same = (A == B);
+  pi.mol = 0;
+  info[t] = pi;
+}
+
+// ------------------------------------------------------------- symmetrise
+// J = 2 (J' + J'^T), K = K' + K'^T in place.
+__global__ void symmetrize_jk(double* __restrict__ J, double* __restrict__ K, int n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long tot = (long long)n * n;
+  if (t >= tot) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  if (j < i) return;
+  const size_t ij = (size_t)i * n + j, ji = (size_t)j * n + i;
+  if (J) {
+    const double s = 2.0 * (J[ij] + J[ji]);
+    J[ij] = s;
+    J[ji] = s;
+  }
+  if (K) {
+    const double s = K[ij] + K[ji];
+    K[ij] = s;
+    K[ji] = s;
+  }
+}
+
+// ------------------------------------------------------------- basis create
+extern "C" int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, const hf_shell* shells, int nshell,
+                               const double* exps, const double* coefs, int n_electrons, hf_basis** out) {
+  if (!out) return hf_fail(HF_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!ctx || !atoms || !shells || !exps || !coefs || natom <= 0 || nshell <= 0)
+    return hf_fail(HF_ERR_INVALID, "hf_basis_create: null or empty input");
+  if (n_electrons < 0) return hf_fail(HF_ERR_INVALID, "negative electron count");
+  if (n_electrons % 2) return hf_fail(HF_ERR_ODD_ELECTRONS, "closed-shell RHF needs an even electron count (%d)", n_electrons);
+  int nprim = 0, nbf = 0, lmax = 0;
+  for (int s = 0; s < nshell; ++s) {
+    const hf_shell& sh = shells[s];
+    if (sh.l < 0) return hf_fail(HF_ERR_INVALID, "shell %d: negative l", s);
+    if (sh.l > HF_LMAX) return hf_fail(HF_ERR_UNSUPPORTED_L, "shell %d: l = %d above %d", s, sh.l, HF_LMAX);
+    if (sh.atom < 0 || sh.atom >= natom) return hf_fail(HF_ERR_INVALID, "shell %d: atom index %d", s, sh.atom);
+    if (sh.nprim < 1 || sh.nprim > HF_MAX_NPRIM) return hf_fail(HF_ERR_INVALID, "shell %d: nprim %d", s, sh.nprim);
+    if (sh.prim_off < 0) return hf_fail(HF_ERR_INVALID, "shell %d: prim_off", s);
+    nprim = std::max(nprim, sh.prim_off + sh.nprim);
+    nbf += ncart(sh.l);
+    lmax = std::max(lmax, sh.l);
+  }
+  for (int k = 0; k < nprim; ++k)
+    if (!(exps[k] > 0.0) || !std::isfinite(exps[k]) || !std::isfinite(coefs[k]))
+      return hf_fail(HF_ERR_INVALID, "primitive %d: exponent must be positive and finite", k);
+  for (int a = 0; a < natom; ++a)
+    for (int x = 0; x < 3; ++x)
+      if (!std::isfinite(atoms[a].xyz[x])) return hf_fail(HF_ERR_INVALID, "atom %d: non-finite coordinate", a);
+
+  cudaSetDevice(ctx->device);
+  hf_basis* b = new (std::nothrow) hf_basis();
+  if (!b) return hf_fail(HF_ERR_OOM, "host allocation");
+  b->ctx = ctx;
+  b->natom = natom;
+  b->nshell = nshell;
+  b->nbf = nbf;
+  b->nprim = nprim;
+  b->nelec = n_electrons;
+  b->lmax = lmax;
+  b->atoms.assign(atoms, atoms + natom);
+  b->sh_atom.resize(nshell);
+  b->sh_l.resize(nshell);
+  b->sh_nprim.resize(nshell);
+  b->sh_prim.resize(nshell);
+  b->sh_bf.resize(nshell + 1);
+  b->exps.assign(exps, exps + nprim);
+  b->coefs.assign(nprim, 0.0);
+  int bf = 0;
+  for (int s = 0; s < nshell; ++s) {
+    b->sh_atom[s] = shells[s].atom;
+    b->sh_l[s] = shells[s].l;
+    b->sh_nprim[s] = shells[s].nprim;
+    b->sh_prim[s] = shells[s].prim_off;
+    b->sh_bf[s] = bf;
+    bf += ncart(shells[s].l);
+  }
+  b->sh_bf[nshell] = bf;
+  // Contracted normalisation (Eq. 1 functions of unit norm): primitive
+  // factors for the axial component x^l, then the contraction rescaled by
+  // its self-overlap.  Other Cartesian components carry comp_scale().
+  for (int s = 0; s < nshell; ++s) {
+    const int l = b->sh_l[s], K = b->sh_nprim[s], p0 = b->sh_prim[s];
+    std::vector<double> c(K);
+    for (int k = 0; k < K; ++k) {
+      const double a = exps[p0 + k];
+      c[k] = coefs[p0 + k] * pow(2.0 * a / kPi, 0.75) * pow(4.0 * a, 0.5 * l) / sqrt(dfact(2 * l - 1));
+    }
+    double self = 0.0;
+    for (int i = 0; i < K; ++i)
+      for (int j = 0; j < K; ++j) {
+        const double p = exps[p0 + i] + exps[p0 + j];
+        self += c[i] * c[j] * pow(kPi / p, 1.5) * dfact(2 * l - 1) / pow(2.0 * p, l);
+      }
+    if (!(self > 0.0)) {
+      delete b;
+      return hf_fail(HF_ERR_INVALID, "shell %d: contraction has zero norm", s);
+    }
+    for (int k = 0; k < K; ++k) b->coefs[p0 + k] = c[k] / sqrt(self);
+  }
+  double en = 0.0;
+  for (int i = 0; i < natom; ++i)
+    for (int j = 0; j < i; ++j) {
+      double r2 = 0.0;
+      for (int x = 0; x < 3; ++x) {
+        const double d = atoms[i].xyz[x] - atoms[j].xyz[x];
+        r2 += d * d;
+      }
+      if (r2 == 0.0 && atoms[i].Z != 0 && atoms[j].Z != 0) {
+        delete b;
+        return hf_fail(HF_ERR_INVALID, "atoms %d and %d coincide", i, j);
+      }
+      if (r2 > 0.0) en += (double)atoms[i].Z * atoms[j].Z / sqrt(r2);
+    }
+  b->e_nuc = en;
+
+  // Shell pairs, grouped by pair class; within a pair l_A >= l_B.
+  std::vector<int> cls_of;
+  for (int i = 0; i < nshell; ++i)
+    for (int j = 0; j <= i; ++j) {
+      int A = i, B = j;
+      if (b->sh_l[B] > b->sh_l[A]) std::swap(A, B);
+      b->pair_A.push_back(A);
+      b->pair_B.push_back(B);
+      cls_of.push_back(pair_class(b->sh_l[A], b->sh_l[B]));
+    }
+  const int np = (int)b->pair_A.size();
+  std::vector<int> idx(np);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cls_of[x] < cls_of[y]; });
+  std::vector<int> pA(np), pB(np), poff(np);
+  int off = 0;
+  {
+    int cnt[HF_NPAIRCLASS] = {};
+    for (int k = 0; k < np; ++k) ++cnt[cls_of[k]];
+    b->class_begin[0] = 0;
+    for (int c = 0; c < HF_NPAIRCLASS; ++c) b->class_begin[c + 1] = b->class_begin[c] + cnt[c];
+  }
+  for (int k = 0; k < np; ++k) {
+    pA[k] = b->pair_A[idx[k]];
+    pB[k] = b->pair_B[idx[k]];
+    poff[k] = off;
+    off += b->sh_nprim[pA[k]] * b->sh_nprim[pB[k]];
+  }
+  b->pair_A = pA;
+  b->pair_B = pB;
+  b->npairs = np;
+  b->nprimpairs = off;
+
+  int rc = HF_OK;
+  std::vector<double> sh_xyz(3 * nshell);
+  for (int s = 0; s < nshell; ++s)
+    for (int x = 0; x < 3; ++x) sh_xyz[3 * s + x] = atoms[b->sh_atom[s]].xyz[x];
+  DevArray<int> dA, dB, dOff, dl, dn, dp, dbf;
+  DevArray<double> dxyz, dexp, dcoef;
+  cudaStream_t st = ctx->stream;
+  do {
+    if ((rc = dA.alloc(ctx, np)) || (rc = dB.alloc(ctx, np)) || (rc = dOff.alloc(ctx, np)) ||
+        (rc = dl.alloc(ctx, nshell)) || (rc = dn.alloc(ctx, nshell)) || (rc = dp.alloc(ctx, nshell)) ||
+        (rc = dbf.alloc(ctx, nshell + 1)) || (rc = dxyz.alloc(ctx, 3 * nshell)) || (rc = dexp.alloc(ctx, nprim)) ||
+        (rc = dcoef.alloc(ctx, nprim)) || (rc = b->prim64.alloc(ctx, (size_t)off * PRIM64_STRIDE)) ||
+        (rc = b->prim32.alloc(ctx, (size_t)off * PRIM32_STRIDE)) || (rc = b->pinfo.alloc(ctx, np)) ||
+        (rc = b->Q.alloc(ctx, np)) || (rc = b->ketlist.alloc(ctx, np)) || (rc = b->counters.alloc(ctx, 2 * HF_NCLASS)))
+      break;
+#define UP(dst, src, cnt)                                                                                      \
+  if (cudaMemcpyAsync(dst.ptr, src, sizeof(*dst.ptr) * (cnt), cudaMemcpyHostToDevice, st) != cudaSuccess) { \
+    rc = hf_fail(HF_ERR_CUDA, "upload");                                                                     \
+    break;                                                                                                   \
+  }
+    UP(dA, pA.data(), np);
+    UP(dB, pB.data(), np);
+    UP(dOff, poff.data(), np);
+    UP(dl, b->sh_l.data(), nshell);
+    UP(dn, b->sh_nprim.data(), nshell);
+    UP(dp, b->sh_prim.data(), nshell);
+    UP(dbf, b->sh_bf.data(), nshell + 1);
+    UP(dxyz, sh_xyz.data(), 3 * nshell);
+    UP(dexp, b->exps.data(), nprim);
+    UP(dcoef, b->coefs.data(), nprim);
+#undef UP
+    pair_kernel<<<(np + 127) / 128, 128, 0, st>>>(np, dA.ptr, dB.ptr, dOff.ptr, dxyz.ptr, dl.ptr, dn.ptr, dp.ptr, dbf.ptr,
+                                                  dexp.ptr, dcoef.ptr, b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr,
+                                                  kPrimEps);
+    if (cudaGetLastError() != cudaSuccess) { rc = hf_fail(HF_ERR_CUDA, "pair_kernel launch"); break; }
+    // Schwarz factors per pair class, using the (X|X) diagonal quartets.
+    DevArray<int> ids;
+    if ((rc = ids.alloc(ctx, np))) break;
+    std::vector<int> iota_h(np);
+    std::iota(iota_h.begin(), iota_h.end(), 0);
+    if (cudaMemcpyAsync(ids.ptr, iota_h.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = hf_fail(HF_ERR_CUDA, "upload");
+      break;
+    }
+    PairSet ps{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
+    KernelCommon kc{ctx->boys64, ctx->boys32, 0};
+    for (int X = 0; X < HF_NPAIRCLASS; ++X) {
+      const int n = b->class_begin[X + 1] - b->class_begin[X];
+      if (n <= 0) continue;
+      ctx->ops[X * (X + 1) / 2 + X].schwarz(ids.ptr + b->class_begin[X], n, ps, kc, b->Q.ptr, st);
+    }
+    if (cudaGetLastError() != cudaSuccess) { rc = hf_fail(HF_ERR_CUDA, "schwarz launch"); break; }
+    b->Q_h.resize(np);
+    std::vector<PairInfo> info_h(np);
+    if (cudaMemcpyAsync(b->Q_h.data(), b->Q.ptr, sizeof(double) * np, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(info_h.data(), b->pinfo.ptr, sizeof(PairInfo) * np, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = hf_fail(HF_ERR_CUDA, "pair setup: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    b->nprim_sig_h.resize(np);
+    for (int k = 0; k < np; ++k) b->nprim_sig_h[k] = info_h[k].nprim;
+    // Ket lists: pairs of each class sorted by Q descending.
+    b->ketlist_h.resize(np);
+    for (int X = 0; X < HF_NPAIRCLASS; ++X) {
+      const int s0 = b->class_begin[X], s1 = b->class_begin[X + 1];
+      for (int k = s0; k < s1; ++k) b->ketlist_h[k] = k;
+      std::stable_sort(b->ketlist_h.begin() + s0, b->ketlist_h.begin() + s1,
+                       [&](int x, int y) { return b->Q_h[x] > b->Q_h[y]; });
+    }
+    if (cudaMemcpyAsync(b->ketlist.ptr, b->ketlist_h.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) {
+      rc = hf_fail(HF_ERR_CUDA, "upload");
+      break;
+    }
+  } while (0);
+  if (rc != HF_OK) {
+    cudaStreamSynchronize(st);
+    hf_basis_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return HF_OK;
+}
+
+extern "C" void hf_basis_destroy(hf_basis* b) {
+  if (!b) return;
+  cudaSetDevice(b->ctx->device);
+  cudaStreamSynchronize(b->ctx->stream);
+  delete b;
+}
+
+extern "C" int hf_basis_nbf(const hf_basis* b) { return b ? b->nbf : 0; }
+extern "C" int hf_basis_nshell(const hf_basis* b) { return b ? b->nshell : 0; }
+
+extern "C" size_t hf_basis_device_bytes(const hf_basis* b) {
+  if (!b) return 0;
+  size_t s = b->prim64.bytes() + b->prim32.bytes() + b->pinfo.bytes() + b->Q.bytes() + b->ketlist.bytes() +
+             b->counters.bytes() + b->hD.bytes() + b->hJ.bytes() + b->hK.bytes() + b->S.bytes() + b->T.bytes() +
+             b->V.bytes();
+  for (int c = 0; c < HF_NCLASS; ++c)
+    for (const ClassWork* w : {&b->work64[c], &b->work32[c]})
+      s += w->bra.bytes() + w->kbeg.bytes() + w->kend.bytes() + w->ioff.bytes();
+  return s;
+}
+
+// ------------------------------------------------------------- Schwarz output
+extern "C" int hf_schwarz(hf_basis* b, double* Q) {
+  if (!b || !Q) return hf_fail(HF_ERR_INVALID, "hf_schwarz: null argument");
+  const int ns = b->nshell;
+  for (int k = 0; k < ns * ns; ++k) Q[k] = 0.0;
+  for (int k = 0; k < b->npairs; ++k) {
+    const int A = b->pair_A[k], B = b->pair_B[k];
+    Q[A * ns + B] = Q[B * ns + A] = b->Q_h[k];
+  }
+  return HF_OK;
+}
+
+// ------------------------------------------------------------- work lists
+// For each canonical class (X|Y), X >= Y: bra entries are the pairs of
+// class X in Q-descending order; for bra i the kept kets are the prefix of
+// the class-Y list with Q_i Q_k >= tau (the Schwarz rule: drop iff
+// Q_ab Q_cd < tau), cut at k <= i when X == Y so each unordered pair of
+// pairs appears once.  The kets with Q_i Q_k >= fp32_bound form the FP64
+// range, the rest the FP32 range.
+int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
+  if (b->have_work && b->work_tau == tau && b->work_fp32 == fp32_bound) return HF_OK;
+  hf_ctx* ctx = b->ctx;
+  cudaStream_t st = ctx->stream;
+  for (int X = 0; X < HF_NPAIRCLASS; ++X)
+    for (int Y = 0; Y <= X; ++Y) {
+      const int cls = X * (X + 1) / 2 + Y;
+      const int xb = b->class_begin[X], xe = b->class_begin[X + 1];
+      const int yb = b->class_begin[Y], ye = b->class_begin[Y + 1];
+      const int ny = ye - yb;
+      std::vector<int> bra[2], kb[2], ke[2], io[2];
+      long long nq[2] = {0, 0};
+      io[0].push_back(0);
+      io[1].push_back(0);
+      for (int i = xb; i < xe; ++i) {
+        const int pi = b->ketlist_h[i];
+        const double qi = b->Q_h[pi];
+        // first k with qi * Q_k < tau (Q descending => monotone)
+        auto count_ge = [&](double thr) {
+          int lo = 0, hi = ny;
+          while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (qi * b->Q_h[b->ketlist_h[yb + mid]] >= thr) lo = mid + 1; else hi = mid;
+          }
+          return lo;
+        };
+        int n = count_ge(tau);
+        if (X == Y) n = std::min(n, i - xb + 1);
+        int m = fp32_bound > 0.0 ? std::min(count_ge(fp32_bound), n) : n;
+        const int lo_[2] = {0, m}, hi_[2] = {m, n};
+        for (int r = 0; r < 2; ++r) {
+          const int cnt = hi_[r] - lo_[r];
+          if (cnt <= 0) continue;
+          bra[r].push_back(pi);
+          kb[r].push_back(lo_[r]);
+          ke[r].push_back(hi_[r]);
+          io[r].push_back(io[r].back() + (cnt + 31) / 32);
+          nq[r] += cnt;
+        }
+      }
+      for (int r = 0; r < 2; ++r) {
+        ClassWork& w = r == 0 ? b->work64[cls] : b->work32[cls];
+        const int nb = (int)bra[r].size();
+        HF_CHECK(w.bra.alloc(ctx, nb));
+        HF_CHECK(w.kbeg.alloc(ctx, nb));
+        HF_CHECK(w.kend.alloc(ctx, nb));
+        HF_CHECK(w.ioff.alloc(ctx, nb + 1));
+        if (nb > 0) {
+          HF_CUDA(cudaMemcpyAsync(w.bra.ptr, bra[r].data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+          HF_CUDA(cudaMemcpyAsync(w.kbeg.ptr, kb[r].data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+          HF_CUDA(cudaMemcpyAsync(w.kend.ptr, ke[r].data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+          HF_CUDA(cudaMemcpyAsync(w.ioff.ptr, io[r].data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
+        }
+        if (io[r].back() > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "class %d: too many work items", cls);
+        w.w.bra = w.bra.ptr;
+        w.w.ket = b->ketlist.ptr + yb;
+        w.w.kbeg = w.kbeg.ptr;
+        w.w.kend = w.kend.ptr;
+        w.w.ioff = w.ioff.ptr;
+        w.w.nbra = nb;
+        w.w.nitems = io[r].back();
+        w.w.counter = b->counters.ptr + 2 * cls + r;
+        w.nquartets = nq[r];
+      }
+    }
+  // host vectors die at return: make sure the uploads have completed
+  HF_CUDA(cudaStreamSynchronize(st));
+  b->have_work = true;
+  b->work_tau = tau;
+  b->work_fp32 = fp32_bound;
+  return HF_OK;
+}
+
+extern "C" int hf_count_quartets(hf_basis* b, const hf_jk_opts* opts, long long* n_total, long long* n_fp32) {
+  if (!b) return hf_fail(HF_ERR_INVALID, "null basis");
+  hf_jk_opts o;
+  hf_jk_opts_default(&o);
+  if (opts) o = *opts;
+  std::lock_guard<std::mutex> lk(b->ctx->mu);
+  cudaSetDevice(b->ctx->device);
+  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound));
+  long long t = 0, f = 0;
+  for (int c = 0; c < HF_NCLASS; ++c) {
+    t += b->work64[c].nquartets + b->work32[c].nquartets;
+    f += b->work32[c].nquartets;
+  }
+  if (n_total) *n_total = t;
+  if (n_fp32) *n_fp32 = f;
+  return HF_OK;
+}
+
+static int launch_grid(hf_ctx* ctx, int occ, int nitems) {
+  const int warps = 4;
+  int g = (nitems + warps - 1) / warps;
+  const int cap = std::max(1, occ) * ctx->num_sms;
+  return std::max(1, std::min(g, cap));
+}
+
+int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts& o, long long* nq) {
+  hf_ctx* ctx = b->ctx;
+  cudaStream_t st = ctx->stream;
+  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound));
+  const size_t nn = (size_t)b->nbf * b->nbf;
+  HF_CUDA(cudaMemsetAsync(J, 0, nn * sizeof(double), st));
+  HF_CUDA(cudaMemsetAsync(K, 0, nn * sizeof(double), st));
+  HF_CUDA(cudaMemsetAsync(b->counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
+  PairSet ps{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
+  KernelCommon kc{ctx->boys64, ctx->boys32, (o.flags & HF_JK_FP32_BOYS) ? 1 : 0};
+  long long total = 0;
+  // heaviest classes first
+  for (int c = HF_NCLASS - 1; c >= 0; --c) {
+    const EriClassOps& op = ctx->ops[c];
+    ClassWork& w64 = b->work64[c];
+    ClassWork& w32 = b->work32[c];
+    const MolJK one{D, J, K, b->nbf, 0};
+    if (w64.w.nitems > 0) op.jk64(w64.w, ps, kc, one, nullptr, launch_grid(ctx, op.occ64(), w64.w.nitems), st);
+    if (w32.w.nitems > 0) op.jk32(w32.w, ps, kc, one, nullptr, launch_grid(ctx, op.occ32(), w32.w.nitems), st);
+    total += w64.nquartets + w32.nquartets;
+  }
+  HF_CUDA(cudaGetLastError());
+  symmetrize_jk<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(J, K, b->nbf);
+  HF_CUDA(cudaGetLastError());
+  if (nq) *nq = total;
+  return HF_OK;
+}
+
+// Operations per primitive quartet outside the VRR: p+q, 1/sqrt, 1/(p+q),
+// rho/p, rho/q, PQ, WP, WQ, T, prefactor (22), the Boys evaluation (Taylor
+// 14 per order for L <= 1; else 14 + exp 18 + 3L), scaling of B (L+1).
+static int prim_overhead_flops(int L) {
+  const int boys = L <= 1 ? 14 * (L + 1) : 14 + 18 + 3 * L;
+  return 22 + boys + (L + 1);
+}
+
+extern "C" int hf_class_stats_get(hf_basis* b, const hf_jk_opts* opts, hf_class_stats* out) {
+  if (!b || !out) return hf_fail(HF_ERR_INVALID, "hf_class_stats_get: null argument");
+  hf_jk_opts o;
+  hf_jk_opts_default(&o);
+  if (opts) o = *opts;
+  std::lock_guard<std::mutex> lk(b->ctx->mu);
+  cudaSetDevice(b->ctx->device);
+  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound));
+  // prefix sums of significant primitive-pair counts along each class's ket list
+  std::vector<long long> pre(b->npairs + 1, 0);
+  for (int k = 0; k < b->npairs; ++k) pre[k + 1] = pre[k] + b->nprim_sig_h[b->ketlist_h[k]];
+  for (int X = 0; X < HF_NPAIRCLASS; ++X)
+    for (int Y = 0; Y <= X; ++Y) {
+      const int c = X * (X + 1) / 2 + Y;
+      hf_class_stats& st = out[c];
+      static const int lx[6] = {0, 1, 1, 2, 2, 2}, ly[6] = {0, 0, 1, 0, 1, 2};
+      st.la = lx[X]; st.lb = ly[X]; st.lc = lx[Y]; st.ld = ly[Y];
+      const EriClassOps& op = b->ctx->ops[c];
+      const int L = st.la + st.lb + st.lc + st.ld;
+      st.vrr_flops = op.vrr_flops;
+      st.hrr_flops = op.hrr_flops;
+      st.prim_flops = op.vrr_flops + prim_overhead_flops(L);
+      const int nblk = ((st.la + 1) * (st.la + 2) / 2) * ((st.lb + 1) * (st.lb + 2) / 2) *
+                       ((st.lc + 1) * (st.lc + 2) / 2) * ((st.ld + 1) * (st.ld + 2) / 2);
+      st.digest_flops = 6 * 2 * nblk;
+      const int yb = b->class_begin[Y];
+      for (int r = 0; r < 2; ++r) {
+        ClassWork& w = r == 0 ? b->work64[c] : b->work32[c];
+        std::vector<int> bra(w.w.nbra), kb(w.w.nbra), ke(w.w.nbra);
+        long long pq = 0;
+        if (w.w.nbra > 0) {
+          HF_CUDA(cudaMemcpy(bra.data(), w.bra.ptr, sizeof(int) * w.w.nbra, cudaMemcpyDeviceToHost));
+          HF_CUDA(cudaMemcpy(kb.data(), w.kbeg.ptr, sizeof(int) * w.w.nbra, cudaMemcpyDeviceToHost));
+          HF_CUDA(cudaMemcpy(ke.data(), w.kend.ptr, sizeof(int) * w.w.nbra, cudaMemcpyDeviceToHost));
+        }
+        for (int i = 0; i < w.w.nbra; ++i)
+          pq += (long long)b->nprim_sig_h[bra[i]] * (pre[yb + ke[i]] - pre[yb + kb[i]]);
+        if (r == 0) { st.quartets_fp64 = w.nquartets; st.prim_quartets_fp64 = pq; }
+        else { st.quartets_fp32 = w.nquartets; st.prim_quartets_fp32 = pq; }
+      }
+    }
+  return HF_OK;
+}
+
+extern "C" int hf_fock_jk_profiled(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts* opts,
+                                   double* class_ms) {
+  if (!b || !D || !J || !K || !class_ms) return hf_fail(HF_ERR_INVALID, "hf_fock_jk_profiled: null argument");
+  hf_jk_opts o;
+  hf_jk_opts_default(&o);
+  if (opts) o = *opts;
+  hf_ctx* ctx = b->ctx;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound));
+  const size_t nn = (size_t)b->nbf * b->nbf;
+  HF_CUDA(cudaMemsetAsync(J, 0, nn * sizeof(double), st));
+  HF_CUDA(cudaMemsetAsync(K, 0, nn * sizeof(double), st));
+  HF_CUDA(cudaMemsetAsync(b->counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
+  PairSet ps{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
+  KernelCommon kc{ctx->boys64, ctx->boys32, (o.flags & HF_JK_FP32_BOYS) ? 1 : 0};
+  const MolJK one{D, J, K, b->nbf, 0};
+  cudaEvent_t ev[2 * HF_NCLASS + 1];
+  for (auto& e : ev) HF_CUDA(cudaEventCreate(&e));
+  int nev = 0;
+  int which[2 * HF_NCLASS];
+  HF_CUDA(cudaEventRecord(ev[nev++], st));
+  for (int c = HF_NCLASS - 1; c >= 0; --c) {
+    const EriClassOps& op = ctx->ops[c];
+    for (int r = 0; r < 2; ++r) {
+      ClassWork& w = r == 0 ? b->work64[c] : b->work32[c];
+      if (w.w.nitems <= 0) continue;
+      (r == 0 ? op.jk64 : op.jk32)(w.w, ps, kc, one, nullptr,
+                                   launch_grid(ctx, r == 0 ? op.occ64() : op.occ32(), w.w.nitems), st);
+      which[nev - 1] = 2 * c + r;
+      HF_CUDA(cudaEventRecord(ev[nev++], st));
+    }
+  }
+  HF_CUDA(cudaGetLastError());
+  symmetrize_jk<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(J, K, b->nbf);
+  HF_CUDA(cudaGetLastError());
+  HF_CUDA(cudaStreamSynchronize(st));
+  for (int k = 0; k < 2 * HF_NCLASS; ++k) class_ms[k] = 0.0;
+  for (int k = 0; k + 1 < nev; ++k) {
+    float ms = 0.f;
+    HF_CUDA(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+    class_ms[which[k]] = ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return HF_OK;
+}
+
+extern "C" int hf_fock_jk(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts* opts) {
+  if (!b || !D || !J || !K) return hf_fail(HF_ERR_INVALID, "hf_fock_jk: null argument");
+  hf_jk_opts o;
+  hf_jk_opts_default(&o);
+  if (opts) o = *opts;
+  if (!(o.schwarz_tau >= 0.0) || !(o.fp32_bound >= 0.0)) return hf_fail(HF_ERR_INVALID, "negative threshold");
+  hf_ctx* ctx = b->ctx;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  const size_t nn = (size_t)b->nbf * b->nbf;
+  if (o.flags & HF_JK_HOST) {
+    if (b->hD.n != nn) {
+      HF_CHECK(b->hD.alloc(ctx, nn));
+      HF_CHECK(b->hJ.alloc(ctx, nn));
+      HF_CHECK(b->hK.alloc(ctx, nn));
+    }
+    HF_CUDA(cudaMemcpyAsync(b->hD.ptr, D, nn * sizeof(double), cudaMemcpyHostToDevice, st));
+    HF_CHECK(hf_fock_jk_device(b, b->hD.ptr, b->hJ.ptr, b->hK.ptr, o, nullptr));
+    HF_CUDA(cudaMemcpyAsync(J, b->hJ.ptr, nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HF_CUDA(cudaMemcpyAsync(K, b->hK.ptr, nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+  } else {
+    HF_CHECK(hf_fock_jk_device(b, D, J, K, o, nullptr));
+  }
+  HF_CUDA(cudaStreamSynchronize(st));
+  return HF_OK;
+}
+
+// ------------------------------------------------------------- ERI tensor
+extern "C" int hf_eri_tensor(hf_basis* b, double* G) {
+  if (!b || !G) return hf_fail(HF_ERR_INVALID, "hf_eri_tensor: null argument");
+  if (b->nbf > 128) return hf_fail(HF_ERR_INVALID, "hf_eri_tensor: nbf %d above 128", b->nbf);
+  hf_ctx* ctx = b->ctx;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  HF_CHECK(hf_eri_tensor_device(b, G));
+  HF_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HF_OK;
+}
+
+int hf_eri_tensor_device(hf_basis* b, double* G) {
+  hf_ctx* ctx = b->ctx;
+  cudaStream_t st = ctx->stream;
+  HF_CHECK(hf_basis_prepare_work(b, 0.0, 0.0));
+  HF_CUDA(cudaMemsetAsync(b->counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
+  PairSet ps{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
+  KernelCommon kc{ctx->boys64, ctx->boys32, 0};
+  for (int c = 0; c < HF_NCLASS; ++c) {
+    ClassWork& w = b->work64[c];
+    if (w.w.nitems > 0) ctx->ops[c].store(w.w, ps, kc, G, b->nbf, launch_grid(ctx, 4, w.w.nitems), st);
+  }
+  HF_CUDA(cudaGetLastError());
+  return HF_OK;
+}
+
+// J_ij = sum_kl G_ijkl D_kl and K_il = sum_jk G_ijkl D_jk: one warp per output element.
+__global__ void jk_stored_kernel(const double* __restrict__ G, const double* __restrict__ D, double* __restrict__ J,
+                                 double* __restrict__ K, int n) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long nn = (long long)n * n;
+  if (w >= 2 * nn) return;
+  const bool isK = w >= nn;
+  const long long e = isK ? w - nn : w;
+  const int i = (int)(e / n), x = (int)(e % n);
+  double s = 0.0;
+  for (long long t = lane; t < nn; t += 32) {
+    const int p = (int)(t / n), q = (int)(t % n);
+    if (!isK) s += G[(((size_t)i * n + x) * n + p) * n + q] * D[(size_t)p * n + q];       // J_ix, (ix|pq) D_pq
+    else s += G[(((size_t)i * n + p) * n + q) * n + x] * D[(size_t)p * n + q];           // K_ix, (ip|qx) D_pq
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) (isK ? K : J)[(size_t)i * n + x] = s;
+}
+
+int hf_jk_stored_device(hf_basis* b, const double* G, const double* D, double* J, double* K) {
+  const long long threads = 2LL * b->nbf * b->nbf * 32;
+  jk_stored_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, b->ctx->stream>>>(G, D, J, K, b->nbf);
+  HF_CUDA(cudaGetLastError());
+  return HF_OK;
+}
+
+extern "C" int hf_jk_stored(hf_basis* b, const double* G, const double* D, double* J, double* K) {
+  if (!b || !G || !D || !J || !K) return hf_fail(HF_ERR_INVALID, "hf_jk_stored: null argument");
+  if (b->nbf > 128) return hf_fail(HF_ERR_INVALID, "hf_jk_stored: nbf %d above 128", b->nbf);
+  hf_ctx* ctx = b->ctx;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  HF_CHECK(hf_jk_stored_device(b, G, D, J, K));
+  HF_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HF_OK;
+}

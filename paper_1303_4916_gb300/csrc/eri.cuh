@@ -1,0 +1,499 @@
+// eri.cuh -- per-class ERI kernels with the fused J/K contraction.
+//
+// One thread evaluates one contracted shell quartet (ab|cd) of Eq. 5; the
+// 32 lanes of a warp share the bra pair (ab) and take 32 consecutive kets
+// (cd) from the Schwarz-sorted ket list.  Per primitive quartet the thread
+// evaluates the Boys function F_m(T), m = 0..L, and the Obara-Saika VRR
+// (generated per class), accumulating [e0|f0]; after the primitive loop the
+// HRR gives the Cartesian block, which is digested straight into J and K
+// (the J/K equation of Sec. "Technical details").
+//
+// Digestion of one unique quartet with block I_abcd and degeneracy weight
+// w = 1 / |stabiliser| (1/2 for each of A==B, C==D, (AB)==(CD)):
+//   J'_ab += w sum_cd I D_cd          J'_cd += w sum_ab I D_ab
+//   K'_ac += w sum_bd I D_bd          K'_ad += w sum_bc I D_bc
+//   K'_bc += w sum_ad I D_ad          K'_bd += w sum_ac I D_ac
+// and at the end J = 2 (J' + J'^T), K = K' + K'^T.  This sums the block
+// over the full 8-member orbit of (ab|cd) under the permutational symmetry
+// of Eq. 5 for a symmetric D.  J'_ab is reduced over the warp with
+// shuffles before one FP64 atomic per element; the other five go out as
+// FP64 atomics per lane.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "eri_classes.cuh"
+#include "hf_device.h"
+
+namespace hfk {
+
+// ------------------------------------------------------------- Boys function
+// Table: row i holds F_m(T_i), m = 0..BOYS_NM-1, then exp(-T_i), with
+// T_i = i * BOYS_H.  For T < BOYS_TMAX: Taylor expansion about the nearest
+// grid point, F_m(T_i - x) = sum_k F_{m+k}(T_i) x^k / k! (since
+// dF_m/dT = -F_{m+1}), 8 terms; exp(-T) = exp(-T_i) exp(x) likewise; then
+// the downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1).  For
+// T >= BOYS_TMAX: F_0 = sqrt(pi/T)/2 and F_{m+1} = (2m+1) F_m / (2T), the
+// neglected exp(-T) terms being below 1e-26.
+template <int L>
+__device__ __forceinline__ void boys64(double T, const double* __restrict__ tab, double* F) {
+  if (T < BOYS_TMAX) {
+    const int i = __double2int_rn(T * (1.0 / BOYS_H));
+    const double x = (double)i * BOYS_H - T;  // T = T_i - x
+    const double* __restrict__ r = tab + i * BOYS_STRIDE;
+    if (L <= 1) {
+#pragma unroll
+      for (int m = 0; m <= L; ++m) {
+        double f = __ldg(r + m + 7);
+#pragma unroll
+        for (int k = 7; k >= 1; --k) f = fma(f, x * (1.0 / k), __ldg(r + m + k - 1));
+        F[m] = f;
+      }
+    } else {
+      double f = __ldg(r + L + 7);
+#pragma unroll
+      for (int k = 7; k >= 1; --k) f = fma(f, x * (1.0 / k), __ldg(r + L + k - 1));
+      F[L] = f;
+      // exp(x), |x| <= BOYS_H/2, 9 terms
+      double e = 1.0 / 40320.0;
+      e = fma(e, x, 1.0 / 5040.0);
+      e = fma(e, x, 1.0 / 720.0);
+      e = fma(e, x, 1.0 / 120.0);
+      e = fma(e, x, 1.0 / 24.0);
+      e = fma(e, x, 1.0 / 6.0);
+      e = fma(e, x, 0.5);
+      e = fma(e, x, 1.0);
+      e = fma(e, x, 1.0);
+      e *= __ldg(r + BOYS_NM);
+      const double t2 = 2.0 * T;
+#pragma unroll
+      for (int m = L - 1; m >= 0; --m) F[m] = fma(t2, F[m + 1], e) * (1.0 / (2 * m + 1));
+    }
+  } else {
+    const double rt = rsqrt(T);
+    const double o2t = 0.5 * rt * rt;
+    F[0] = 0.88622692545275801365 * rt;  // sqrt(pi)/2
+#pragma unroll
+    for (int m = 0; m < L; ++m) F[m + 1] = F[m] * ((2 * m + 1) * o2t);
+  }
+}
+
+// FP32 evaluation of the same expansion, 5 terms (truncation below 3e-9
+// relative), for the reduced-precision quartets when requested.
+template <int L>
+__device__ __forceinline__ void boys32(float T, const float* __restrict__ tab, float* F) {
+  if (T < (float)BOYS_TMAX) {
+    const int i = __float2int_rn(T * (float)(1.0 / BOYS_H));
+    const float x = (float)i * (float)BOYS_H - T;
+    const float* __restrict__ r = tab + i * BOYS_STRIDE;
+    if (L <= 1) {
+#pragma unroll
+      for (int m = 0; m <= L; ++m) {
+        float f = __ldg(r + m + 4);
+#pragma unroll
+        for (int k = 4; k >= 1; --k) f = fmaf(f, x * (1.0f / k), __ldg(r + m + k - 1));
+        F[m] = f;
+      }
+    } else {
+      float f = __ldg(r + L + 4);
+#pragma unroll
+      for (int k = 4; k >= 1; --k) f = fmaf(f, x * (1.0f / k), __ldg(r + L + k - 1));
+      F[L] = f;
+      float e = 1.0f / 120.0f;
+      e = fmaf(e, x, 1.0f / 24.0f);
+      e = fmaf(e, x, 1.0f / 6.0f);
+      e = fmaf(e, x, 0.5f);
+      e = fmaf(e, x, 1.0f);
+      e = fmaf(e, x, 1.0f);
+      e *= __ldg(r + BOYS_NM);
+      const float t2 = 2.0f * T;
+#pragma unroll
+      for (int m = L - 1; m >= 0; --m) F[m] = fmaf(t2, F[m + 1], e) * (1.0f / (2 * m + 1));
+    }
+  } else {
+    const float rt = rsqrtf(T);
+    const float o2t = 0.5f * rt * rt;
+    F[0] = 0.88622692545275801365f * rt;
+#pragma unroll
+    for (int m = 0; m < L; ++m) F[m + 1] = F[m] * ((2 * m + 1) * o2t);
+  }
+}
+
+// ------------------------------------------------------------- primitive pairs
+template <typename R>
+struct Prim {
+  R p, o2p, P[3], PA[3], K;
+};
+
+__device__ __forceinline__ void load_prim(const double* __restrict__ base, int idx, Prim<double>& q) {
+  const double2* s = reinterpret_cast<const double2*>(base + (size_t)idx * PRIM64_STRIDE);
+  const double2 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2), d = __ldg(s + 3), e = __ldg(s + 4);
+  q.p = a.x; q.o2p = a.y; q.P[0] = b.x; q.P[1] = b.y; q.P[2] = c.x;
+  q.PA[0] = c.y; q.PA[1] = d.x; q.PA[2] = d.y; q.K = e.x;
+}
+
+__device__ __forceinline__ void load_prim(const float* __restrict__ base, int idx, Prim<float>& q) {
+  const float4* s = reinterpret_cast<const float4*>(base + (size_t)idx * PRIM32_STRIDE);
+  const float4 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2);
+  q.p = a.x; q.o2p = a.y; q.P[0] = a.z; q.P[1] = a.w; q.P[2] = b.x;
+  q.PA[0] = b.y; q.PA[1] = b.z; q.PA[2] = b.w; q.K = c.x;
+}
+
+template <typename R> struct PrimBase;
+template <> struct PrimBase<double> { static __device__ __forceinline__ const double* get(const PairSet& s) { return s.prim64; } };
+template <> struct PrimBase<float> { static __device__ __forceinline__ const float* get(const PairSet& s) { return s.prim32; } };
+
+template <int L, typename R>
+struct BoysSel {
+  static __device__ __forceinline__ void eval(R T, const KernelCommon& kc, R* F);
+};
+template <int L>
+struct BoysSel<L, double> {
+  static __device__ __forceinline__ void eval(double T, const KernelCommon& kc, double* F) {
+    boys64<L>(T, kc.boys64, F);
+  }
+};
+template <int L>
+struct BoysSel<L, float> {
+  // Reduced-precision quartets: F_m in FP64 (table + downward recursion),
+  // rounded to FP32 for the recurrences, unless boys_fp32 is set.
+  static __device__ __forceinline__ void eval(float T, const KernelCommon& kc, float* F) {
+    if (kc.boys_fp32) {
+      boys32<L>(T, kc.boys32, F);
+    } else {
+      double Fd[L + 1];
+      boys64<L>((double)T, kc.boys64, Fd);
+#pragma unroll
+      for (int m = 0; m <= L; ++m) F[m] = (float)Fd[m];
+    }
+  }
+};
+
+// Contracted block of one shell quartet: loops over the significant
+// primitive pairs of bra and ket.  nb/nk are the primitive-pair counts
+// (0 for an inactive lane).
+template <class C, typename R>
+__device__ __forceinline__ void contracted_vrr(const PairSet& ps, const KernelCommon& kc, int b0, int nb,
+                                               int k0, int nk, R* acc) {
+  const auto* base = PrimBase<R>::get(ps);
+#pragma unroll
+  for (int x = 0; x < C::NE * C::NF; ++x) acc[x] = (R)0;
+  for (int ib = 0; ib < nb; ++ib) {
+    Prim<R> a;
+    load_prim(base, b0 + ib, a);
+    for (int ik = 0; ik < nk; ++ik) {
+      Prim<R> c;
+      load_prim(base, k0 + ik, c);
+      const R pq = a.p + c.p;
+      const R rs = (R)rsqrt(pq);
+      const R inv = rs * rs;
+      const R rp = c.p * inv;  // rho / zeta
+      const R rq = a.p * inv;  // rho / eta
+      R PQ[3], WP[3], WQ[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        PQ[i] = a.P[i] - c.P[i];
+        WP[i] = -rp * PQ[i];
+        WQ[i] = rq * PQ[i];
+      }
+      const R T = a.p * rp * (PQ[0] * PQ[0] + PQ[1] * PQ[1] + PQ[2] * PQ[2]);
+      R B[C::L + 1];
+      BoysSel<C::L, R>::eval(T, kc, B);
+      const R pref = a.K * c.K * rs;
+#pragma unroll
+      for (int m = 0; m <= C::L; ++m) B[m] *= pref;
+      C::template vrr<R>(acc, B, a.PA, WP, c.PA, WQ, a.o2p, c.o2p, (R)0.5 * inv, rp, rq);
+    }
+  }
+}
+
+// Cartesian component scale of a d function relative to the axial one
+// (xy, xz, yz carry sqrt(3)); s and p components are 1.
+__device__ __forceinline__ constexpr double comp_scale(int l, int c) {
+  return (l == 2 && (c == 1 || c == 2 || c == 4)) ? 1.7320508075688772935 : 1.0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------- J/K kernel
+// items: work item t covers bra list entry bi (found by binary search in
+// ioff) and kets kbeg[bi] + 32*(t - ioff[bi]) + lane of the ket list.
+// one: D/J/K of a single molecule; mols (if not null): per-molecule table
+// indexed by PairInfo::mol for a multi-molecule arena.
+template <class C, typename R>
+__global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairSet ps, const KernelCommon kc,
+                                                     const MolJK one, const MolJK* __restrict__ mols) {
+  constexpr int NA = C::NA, NB = C::NB, NC = C::NC, ND = C::ND;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(w.counter, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= w.nitems) break;
+    int lo = 0, hi = w.nbra;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(w.ioff + mid) <= t) lo = mid; else hi = mid;
+    }
+    const int bi = lo;
+    const int bp = __ldg(w.bra + bi);
+    const int kidx = __ldg(w.kbeg + bi) + 32 * (t - __ldg(w.ioff + bi)) + lane;
+    const bool active = kidx < __ldg(w.kend + bi);
+    const int kp = active ? __ldg(w.ket + kidx) : bp;
+    const PairInfo bra = ps.info[bp];
+    const PairInfo ket = ps.info[kp];
+
+    R acc[C::NE * C::NF];
+    contracted_vrr<C, R>(ps, kc, bra.prim0, bra.nprim, ket.prim0, active ? ket.nprim : 0, acc);
+    R I[NA * NB * NC * ND];
+    {
+      R AB[3] = {(R)bra.AB[0], (R)bra.AB[1], (R)bra.AB[2]};
+      R CD[3] = {(R)ket.AB[0], (R)ket.AB[1], (R)ket.AB[2]};
+      C::template hrr<R>(acc, I, AB, CD);
+    }
+    const MolJK mj = mols ? mols[bra.mol] : one;
+    const double* __restrict__ D = mj.D;
+    double* __restrict__ J = mj.J;
+    double* __restrict__ Kx = mj.K;
+    const int nbf = mj.nbf;
+    double wdeg = active ? 1.0 : 0.0;
+    if (bra.same) wdeg *= 0.5;
+    if (ket.same) wdeg *= 0.5;
+    if (bp == kp) wdeg *= 0.5;
+
+    const int a0 = bra.bfA, b0 = bra.bfB, c0 = ket.bfA, d0 = ket.bfB;
+    // J'_ab = w sum_cd I D_cd  (warp-reduced: the bra is uniform over the warp)
+    double Dcd[NC * ND];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int d = 0; d < ND; ++d)
+        Dcd[c * ND + d] = active ? __ldg(D + (size_t)(c0 + c) * nbf + d0 + d) * comp_scale(C::LC, c) * comp_scale(C::LD, d) : 0.0;
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        double s = 0.0;
+#pragma unroll
+        for (int cd = 0; cd < NC * ND; ++cd) s = fma((double)I[(a * NB + b) * NC * ND + cd], Dcd[cd], s);
+        s = warp_sum(s * wdeg);
+        if (lane == 0 && s != 0.0)
+          atomicAdd(J + (size_t)(a0 + a) * nbf + b0 + b, s * comp_scale(C::LA, a) * comp_scale(C::LB, b));
+      }
+    if (!active) continue;
+    // J'_cd = w sum_ab I D_ab
+    double Dab[NA * NB];
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        Dab[a * NB + b] = __ldg(D + (size_t)(a0 + a) * nbf + b0 + b) * comp_scale(C::LA, a) * comp_scale(C::LB, b);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        double s = 0.0;
+#pragma unroll
+        for (int ab = 0; ab < NA * NB; ++ab) s = fma((double)I[ab * NC * ND + c * ND + d], Dab[ab], s);
+        atomicAdd(J + (size_t)(c0 + c) * nbf + d0 + d, s * wdeg * comp_scale(C::LC, c) * comp_scale(C::LD, d));
+      }
+    // K'_ac = w sum_bd I D_bd ;  K'_ad = w sum_bc I D_bc
+    {
+      double Dbd[NB * ND], Dbc[NB * NC];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+          Dbd[b * ND + d] = __ldg(D + (size_t)(b0 + b) * nbf + d0 + d) * comp_scale(C::LB, b) * comp_scale(C::LD, d);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          Dbc[b * NC + c] = __ldg(D + (size_t)(b0 + b) * nbf + c0 + c) * comp_scale(C::LB, b) * comp_scale(C::LC, c);
+      }
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          double s = 0.0;
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int d = 0; d < ND; ++d) s = fma((double)I[((a * NB + b) * NC + c) * ND + d], Dbd[b * ND + d], s);
+          atomicAdd(Kx + (size_t)(a0 + a) * nbf + c0 + c, s * wdeg * comp_scale(C::LA, a) * comp_scale(C::LC, c));
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          double s = 0.0;
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) s = fma((double)I[((a * NB + b) * NC + c) * ND + d], Dbc[b * NC + c], s);
+          atomicAdd(Kx + (size_t)(a0 + a) * nbf + d0 + d, s * wdeg * comp_scale(C::LA, a) * comp_scale(C::LD, d));
+        }
+      }
+    }
+    // K'_bc = w sum_ad I D_ad ;  K'_bd = w sum_ac I D_ac
+    {
+      double Dad[NA * ND], Dac[NA * NC];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+          Dad[a * ND + d] = __ldg(D + (size_t)(a0 + a) * nbf + d0 + d) * comp_scale(C::LA, a) * comp_scale(C::LD, d);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          Dac[a * NC + c] = __ldg(D + (size_t)(a0 + a) * nbf + c0 + c) * comp_scale(C::LA, a) * comp_scale(C::LC, c);
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          double s = 0.0;
+#pragma unroll
+          for (int a = 0; a < NA; ++a)
+#pragma unroll
+            for (int d = 0; d < ND; ++d) s = fma((double)I[((a * NB + b) * NC + c) * ND + d], Dad[a * ND + d], s);
+          atomicAdd(Kx + (size_t)(b0 + b) * nbf + c0 + c, s * wdeg * comp_scale(C::LB, b) * comp_scale(C::LC, c));
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          double s = 0.0;
+#pragma unroll
+          for (int a = 0; a < NA; ++a)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) s = fma((double)I[((a * NB + b) * NC + c) * ND + d], Dac[a * NC + c], s);
+          atomicAdd(Kx + (size_t)(b0 + b) * nbf + d0 + d, s * wdeg * comp_scale(C::LB, b) * comp_scale(C::LD, d));
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- ERI tensor kernel
+// Same work decomposition; every element of the block is written to all
+// eight index permutations of the dense nbf^4 tensor G (small bases).
+template <class C>
+__global__ void __launch_bounds__(128) eri_store_kernel(const JKWork w, const PairSet ps, const KernelCommon kc,
+                                                        double* __restrict__ G, int nbf) {
+  constexpr int NA = C::NA, NB = C::NB, NC = C::NC, ND = C::ND;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(w.counter, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= w.nitems) break;
+    int lo = 0, hi = w.nbra;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(w.ioff + mid) <= t) lo = mid; else hi = mid;
+    }
+    const int bi = lo;
+    const int bp = __ldg(w.bra + bi);
+    const int kidx = __ldg(w.kbeg + bi) + 32 * (t - __ldg(w.ioff + bi)) + lane;
+    if (kidx >= __ldg(w.kend + bi)) continue;
+    const int kp = __ldg(w.ket + kidx);
+    const PairInfo bra = ps.info[bp];
+    const PairInfo ket = ps.info[kp];
+    double acc[C::NE * C::NF];
+    contracted_vrr<C, double>(ps, kc, bra.prim0, bra.nprim, ket.prim0, ket.nprim, acc);
+    double I[NA * NB * NC * ND];
+    C::template hrr<double>(acc, I, bra.AB, ket.AB);
+    const size_t n = (size_t)nbf;
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int d = 0; d < ND; ++d) {
+            const double v = I[((a * NB + b) * NC + c) * ND + d] * comp_scale(C::LA, a) * comp_scale(C::LB, b) *
+                             comp_scale(C::LC, c) * comp_scale(C::LD, d);
+            const size_t i = bra.bfA + a, j = bra.bfB + b, k = ket.bfA + c, l = ket.bfB + d;
+            G[((i * n + j) * n + k) * n + l] = v;
+            G[((j * n + i) * n + k) * n + l] = v;
+            G[((i * n + j) * n + l) * n + k] = v;
+            G[((j * n + i) * n + l) * n + k] = v;
+            G[((k * n + l) * n + i) * n + j] = v;
+            G[((l * n + k) * n + i) * n + j] = v;
+            G[((k * n + l) * n + j) * n + i] = v;
+            G[((l * n + k) * n + j) * n + i] = v;
+          }
+  }
+}
+
+// ------------------------------------------------------------- Schwarz kernel
+// Q_ab = sqrt(max over components |(ab|ab)|) for the pairs of one class;
+// one thread per pair (bra = ket), pairs[] lists the pair ids.
+template <class C>
+__global__ void __launch_bounds__(128) eri_schwarz_kernel(const int* __restrict__ pairs, int npairs, const PairSet ps,
+                                                          const KernelCommon kc, double* __restrict__ Q) {
+  constexpr int NA = C::NA, NB = C::NB;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npairs) return;
+  const int pid = pairs[t];
+  const PairInfo pr = ps.info[pid];
+  double acc[C::NE * C::NF];
+  contracted_vrr<C, double>(ps, kc, pr.prim0, pr.nprim, pr.prim0, pr.nprim, acc);
+  double I[NA * NB * NA * NB];
+  C::template hrr<double>(acc, I, pr.AB, pr.AB);
+  double m = 0.0;
+#pragma unroll
+  for (int a = 0; a < NA; ++a)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const double s = comp_scale(C::LA, a) * comp_scale(C::LB, b);
+      const double v = fabs(I[((a * NB + b) * NA + a) * NB + b]) * s * s;
+      m = v > m ? v : m;
+    }
+  Q[pid] = sqrt(m);
+}
+
+}  // namespace hfk
+
+// Instantiate the launchers of one class into the dispatch table entry.
+#define HF_DEFINE_CLASS_LAUNCHERS(CLS)                                                                   \
+  static void launch_jk64_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one, \
+                                const MolJK* mols, int grid, cudaStream_t s) {                           \
+    hfk::eri_jk_kernel<hfgen::CLS, double><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                   \
+  }                                                                                                      \
+  static void launch_jk32_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one, \
+                                const MolJK* mols, int grid, cudaStream_t s) {                           \
+    hfk::eri_jk_kernel<hfgen::CLS, float><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                    \
+  }                                                                                                      \
+  static void launch_store_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, double* G,   \
+                                 int nbf, int grid, cudaStream_t s) {                                    \
+    hfk::eri_store_kernel<hfgen::CLS><<<grid, 128, 0, s>>>(w, ps, kc, G, nbf);                           \
+  }                                                                                                      \
+  static void launch_schwarz_##CLS(const int* pairs, int npairs, const PairSet& ps, const KernelCommon& kc, \
+                                   double* Q, cudaStream_t s) {                                          \
+    if (npairs > 0)                                                                                      \
+      hfk::eri_schwarz_kernel<hfgen::CLS><<<(npairs + 127) / 128, 128, 0, s>>>(pairs, npairs, ps, kc, Q); \
+  }                                                                                                      \
+  static int occ_jk64_##CLS() {                                                                          \
+    int n = 0;                                                                                           \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hfk::eri_jk_kernel<hfgen::CLS, double>, 128, 0);   \
+    return n;                                                                                            \
+  }                                                                                                      \
+  static int occ_jk32_##CLS() {                                                                          \
+    int n = 0;                                                                                           \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hfk::eri_jk_kernel<hfgen::CLS, float>, 128, 0);    \
+    return n;                                                                                            \
+  }
+
+#define HF_REGISTER_CLASS(table, CLS, la, lb, lc, ld, vf, hf_)                                           \
+  do {                                                                                                   \
+    EriClassOps& e = table[class_index(la, lb, lc, ld)];                                                 \
+    e.jk64 = launch_jk64_##CLS;                                                                          \
+    e.jk32 = launch_jk32_##CLS;                                                                          \
+    e.store = launch_store_##CLS;                                                                        \
+    e.schwarz = launch_schwarz_##CLS;                                                                    \
+    e.occ64 = occ_jk64_##CLS;                                                                            \
+    e.occ32 = occ_jk32_##CLS;                                                                            \
+    e.vrr_flops = vf;                                                                                    \
+    e.hrr_flops = hf_;                                                                                   \
+    e.name = #CLS;                                                                                       \
+  } while (0)

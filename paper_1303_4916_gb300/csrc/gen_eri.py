@@ -1,0 +1,292 @@
+#!/usr/bin/env python3
+"""Generate the per-class recurrence code for the ERI kernels.
+
+For every canonical shell-quartet class (la lb | lc ld) with la >= lb,
+lc >= ld and pair class (la,lb) >= (lc,ld), emit a struct with
+
+* ``vrr``: the Obara-Saika vertical recurrence, in the Head-Gordon-Pople
+  arrangement, from [00|00]^(m) = B_m (prefactor times the Boys function
+  F_m(T)) to the primitive integrals [e0|f0]^(0) for la <= |e| <= la+lb,
+  lc <= |f| <= lc+ld, which it adds into the contracted accumulators;
+
+      [e+1_i,0|00]^(m) = PA_i [e0|00]^(m) + WP_i [e0|00]^(m+1)
+                         + e_i/(2 zeta) ([e-1_i,0|00]^(m) - rho/zeta [e-1_i,0|00]^(m+1))
+      [e0|f+1_i,0]^(m) = QC_i [e0|f0]^(m) + WQ_i [e0|f0]^(m+1)
+                         + f_i/(2 eta) ([e0|f-1_i,0]^(m) - rho/eta [e0|f-1_i,0]^(m+1))
+                         + e_i/(2(zeta+eta)) [e-1_i,0|f0]^(m+1)
+
+* ``hrr``: the horizontal recurrence on the contracted integrals, first on
+  the bra then on the ket,
+
+      (a, b+1_i| = (a+1_i, b| + AB_i (a, b|     (AB = A - B)
+      |c, d+1_i) = |c+1_i, d) + CD_i |c, d)     (CD = C - D)
+
+  writing the Cartesian block out[((a*NB + b)*NC + c)*ND + d].
+
+The recurrences are the closed-form relations between Gaussian integrals
+(Obara & Saika 1986; Head-Gordon & Pople 1988) that the paper's ERI, Eq. 5,
+admits; the paper itself evaluates them by Rys quadrature.  Exact operation
+counts are written next to each class for the roofline accounting.
+
+Usage: gen_eri.py OUT_HEADER [LMAX]
+"""
+from __future__ import annotations
+
+import sys
+
+
+def cart(l):
+    out = []
+    for x in range(l, -1, -1):
+        for y in range(l - x, -1, -1):
+            out.append((x, y, l - x - y))
+    return out
+
+
+def ncart(l):
+    return (l + 1) * (l + 2) // 2
+
+
+def tl(v):
+    return sum(v)
+
+
+def add(v, i, k):
+    w = list(v)
+    w[i] += k
+    return tuple(w)
+
+
+def pick_axis(v):
+    # the axis with the largest power; ties broken towards x
+    best = 0
+    for i in range(3):
+        if v[i] > v[best]:
+            best = i
+    return best
+
+
+class Range:
+    """Cartesian components of all l in [lo, hi], concatenated."""
+
+    def __init__(self, lo, hi):
+        self.lo, self.hi = lo, hi
+        self.comps = []
+        for l in range(lo, hi + 1):
+            self.comps.extend(cart(l))
+        self.index = {c: k for k, c in enumerate(self.comps)}
+
+    def __len__(self):
+        return len(self.comps)
+
+
+class VRR:
+    def __init__(self, la, lb, lc, ld):
+        self.L = la + lb + lc + ld
+        self.E = Range(la, la + lb)
+        self.F = Range(lc, lc + ld)
+        self.memo = {}
+        self.lines = []
+        self.nvar = 0
+        self.flops = 0
+
+    def get(self, e, f, m):
+        key = (e, f, m)
+        if key in self.memo:
+            return self.memo[key]
+        if tl(e) == 0 and tl(f) == 0:
+            name = f"B[{m}]"
+            self.memo[key] = name
+            return name
+        terms = []
+        if tl(f) > 0:
+            i = pick_axis(f)
+            f1 = add(f, i, -1)
+            terms.append(f"QC[{i}] * {self.get(e, f1, m)}")
+            terms.append(f"WQ[{i}] * {self.get(e, f1, m + 1)}")
+            nflop = 3
+            if f1[i] > 0:
+                f2 = add(f1, i, -1)
+                terms.append(f"(R){f1[i]} * o2q * ({self.get(e, f2, m)} - rq * {self.get(e, f2, m + 1)})")
+                nflop += 4
+            if e[i] > 0:
+                e1 = add(e, i, -1)
+                terms.append(f"(R){e[i]} * o2pq * {self.get(e1, f1, m + 1)}")
+                nflop += 3
+        else:
+            i = pick_axis(e)
+            e1 = add(e, i, -1)
+            terms.append(f"PA[{i}] * {self.get(e1, f, m)}")
+            terms.append(f"WP[{i}] * {self.get(e1, f, m + 1)}")
+            nflop = 3
+            if e1[i] > 0:
+                e2 = add(e1, i, -1)
+                terms.append(f"(R){e1[i]} * o2p * ({self.get(e2, f, m)} - rp * {self.get(e2, f, m + 1)})")
+                nflop += 4
+        name = f"v{self.nvar}"
+        self.nvar += 1
+        self.lines.append(f"const R {name} = {' + '.join(terms)};")
+        self.flops += nflop
+        self.memo[key] = name
+        return name
+
+    def build(self):
+        acc_lines = []
+        for fi, f in enumerate(self.F.comps):
+            for ei, e in enumerate(self.E.comps):
+                v = self.get(e, f, 0)
+                acc_lines.append(f"acc[{ei * len(self.F) + fi}] += {v};")
+        self.flops += len(acc_lines)
+        return self.lines + acc_lines
+
+
+class HRR:
+    def __init__(self, la, lb, lc, ld):
+        self.la, self.lb, self.lc, self.ld = la, lb, lc, ld
+        self.E = Range(la, la + lb)
+        self.F = Range(lc, lc + ld)
+        self.flops = 0
+
+    def _side(self, l1, l2, leaf, tmp_prefix, dvec):
+        memo = {}
+        lines = []
+        cnt = [0]
+        flops = [0]
+
+        def get(a, b):
+            key = (a, b)
+            if key in memo:
+                return memo[key]
+            if tl(b) == 0:
+                memo[key] = leaf(a)
+                return memo[key]
+            i = pick_axis(b)
+            b1 = add(b, i, -1)
+            x = get(add(a, i, 1), b1)
+            y = get(a, b1)
+            name = f"{tmp_prefix}{cnt[0]}"
+            cnt[0] += 1
+            lines.append(f"const R {name} = {x} + {dvec}[{i}] * {y};")
+            flops[0] += 2
+            memo[key] = name
+            return name
+
+        outs = []
+        for a in cart(l1):
+            for b in cart(l2):
+                outs.append(get(a, b))
+        return lines, outs, flops[0]
+
+    def build(self):
+        NE, NF = len(self.E), len(self.F)
+        NA, NB, NC, ND = ncart(self.la), ncart(self.lb), ncart(self.lc), ncart(self.ld)
+        code = []
+        # bra: hb[ab * NF + f] from acc[e * NF + f]
+        lines, outs, fl = self._side(self.la, self.lb, lambda a: f"acc[{self.E.index[a]} * {NF} + f]",
+                                     "h", "AB")
+        code.append(f"#pragma unroll")
+        code.append(f"for (int f = 0; f < {NF}; ++f) {{")
+        code += ["  " + s for s in lines]
+        for k, o in enumerate(outs):
+            code.append(f"  hb[{k} * {NF} + f] = {o};")
+        code.append("}")
+        self.flops += fl * NF
+        # ket: out[ab * NC*ND + cd] from hb[ab * NF + f]
+        lines, outs, fl = self._side(self.lc, self.ld, lambda c: f"hb[ab * {NF} + {self.F.index[c]}]",
+                                     "k", "CD")
+        code.append(f"#pragma unroll")
+        code.append(f"for (int ab = 0; ab < {NA * NB}; ++ab) {{")
+        code += ["  " + s for s in lines]
+        for k, o in enumerate(outs):
+            code.append(f"  out[ab * {NC * ND} + {k}] = {o};")
+        code.append("}")
+        self.flops += fl * NA * NB
+        return code
+
+
+LNAME = "spdfghik"
+
+
+def classes(lmax):
+    pairs = [(a, b) for a in range(lmax + 1) for b in range(a + 1)]   # pair classes, ordered
+    out = []
+    for bi, (la, lb) in enumerate(pairs):
+        for ki, (lc, ld) in enumerate(pairs[: bi + 1]):
+            out.append((la, lb, lc, ld))
+    return pairs, out
+
+
+def emit(lmax):
+    pairs, cls = classes(lmax)
+    o = []
+    o.append("// Generated by gen_eri.py -- do not edit by hand.")
+    o.append("// Obara-Saika VRR (Head-Gordon-Pople arrangement) and HRR per class.")
+    o.append("#pragma once")
+    o.append(f"#define HF_GEN_LMAX {lmax}")
+    o.append(f"#define HF_GEN_NPAIRCLASS {len(pairs)}")
+    o.append(f"#define HF_GEN_NCLASS {len(cls)}")
+    o.append("")
+    o.append("namespace hfgen {")
+    o.append("")
+    table = []
+    for (la, lb, lc, ld) in cls:
+        v = VRR(la, lb, lc, ld)
+        vlines = v.build()
+        h = HRR(la, lb, lc, ld)
+        hlines = h.build()
+        NE, NF = len(v.E), len(v.F)
+        name = f"C_{LNAME[la]}{LNAME[lb]}_{LNAME[lc]}{LNAME[ld]}"
+        table.append((name, la, lb, lc, ld, v.flops, h.flops))
+        o.append(f"// ({LNAME[la]}{LNAME[lb]}|{LNAME[lc]}{LNAME[ld]}): VRR {v.flops} flops per primitive "
+                 f"quartet, HRR {h.flops} flops per contracted quartet")
+        o.append(f"struct {name} {{")
+        o.append(f"  static constexpr int LA = {la}, LB = {lb}, LC = {lc}, LD = {ld}, L = {la + lb + lc + ld};")
+        o.append(f"  static constexpr int NE = {NE}, NF = {NF};")
+        o.append(f"  static constexpr int NA = {ncart(la)}, NB = {ncart(lb)}, NC = {ncart(lc)}, ND = {ncart(ld)};")
+        o.append(f"  static constexpr int VRR_FLOPS = {v.flops}, HRR_FLOPS = {h.flops};")
+        o.append("  template <typename R>")
+        o.append("  __device__ __forceinline__ static void vrr(R* __restrict__ acc, const R* __restrict__ B,")
+        o.append("      const R* PA, const R* WP, const R* QC, const R* WQ,")
+        o.append("      R o2p, R o2q, R o2pq, R rp, R rq) {")
+        o.append("    (void)PA; (void)WP; (void)QC; (void)WQ; (void)o2p; (void)o2q; (void)o2pq; (void)rp; (void)rq;")
+        o += ["    " + s for s in vlines]
+        o.append("  }")
+        o.append("  template <typename R>")
+        o.append("  __device__ __forceinline__ static void hrr(const R* __restrict__ acc, R* __restrict__ out,")
+        o.append("      const R* AB, const R* CD) {")
+        o.append("    (void)AB; (void)CD;")
+        if lb == 0 and ld == 0:
+            o.append(f"    #pragma unroll")
+            o.append(f"    for (int x = 0; x < {NE * NF}; ++x) out[x] = acc[x];")
+        else:
+            o.append(f"    R hb[{ncart(la) * ncart(lb) * NF}];")
+            o += ["    " + s for s in hlines]
+        o.append("  }")
+        o.append("};")
+        o.append("")
+    o.append("}  // namespace hfgen")
+    o.append("")
+    o.append("// name, la, lb, lc, ld, VRR flops / primitive quartet, HRR flops / contracted quartet")
+    o.append("#define HF_GEN_CLASS_TABLE(X) \\")
+    for k, (name, la, lb, lc, ld, vf, hf) in enumerate(table):
+        sep = " \\" if k + 1 < len(table) else ""
+        o.append(f"  X({name}, {la}, {lb}, {lc}, {ld}, {vf}, {hf}){sep}")
+    o.append("")
+    return "\n".join(o)
+
+
+def main():
+    out = sys.argv[1]
+    lmax = int(sys.argv[2]) if len(sys.argv) > 2 else 2
+    txt = emit(lmax)
+    try:
+        old = open(out).read()
+    except OSError:
+        old = None
+    if old != txt:
+        with open(out, "w") as fh:
+            fh.write(txt)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,103 @@
+// hf_device.h -- data layouts shared by the host runtime and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// Boys table: rows T_i = i * BOYS_H for i = 0 .. BOYS_NGRID-1; each row
+// holds F_0..F_{BOYS_NM-1}(T_i) and exp(-T_i).  Lookups use the nearest
+// row, so T < BOYS_TMAX keeps the row index inside the table.
+#define BOYS_H 0.1
+#define BOYS_NGRID 602
+#define BOYS_TMAX 60.0
+#define BOYS_NM 16
+#define BOYS_STRIDE (BOYS_NM + 1)
+
+// Primitive-pair record, FP64: p, 1/(2p), P[3], PA[3], K, pad (80 bytes);
+// FP32: the same nine values then three pads (48 bytes).
+// K = c_a c_b exp(-ab/p |AB|^2) sqrt(2) pi^(5/4) / p, so that the
+// primitive-quartet prefactor 2 pi^(5/2) / (p q sqrt(p+q)) K_ab K_cd of
+// [00|00]^(m) is K_ab' K_cd' / sqrt(p+q).
+#define PRIM64_STRIDE 10
+#define PRIM32_STRIDE 12
+
+// Shell pair (A, B) with l_A >= l_B: first basis functions of A and B,
+// offset and count of its significant primitive pairs (sorted by
+// magnitude), AB = A - B, same = (A == B), mol = molecule of the pair in a
+// multi-molecule arena (0 for a single basis).
+struct PairInfo {
+  int bfA, bfB, prim0, nprim;
+  double AB[3];
+  int same, mol;
+};
+
+// Density and J/K outputs of one molecule (device, nbf x nbf row-major).
+struct MolJK {
+  const double* D;
+  double* J;
+  double* K;
+  int nbf;
+  int pad;
+};
+
+struct PairSet {
+  const double* prim64;
+  const float* prim32;
+  const PairInfo* info;
+};
+
+struct KernelCommon {
+  const double* boys64;
+  const float* boys32;
+  int boys_fp32;  // evaluate F_m in FP32 for reduced-precision quartets
+};
+
+// Work list of one (class, precision) launch.
+struct JKWork {
+  const int* bra;   // [nbra] bra pair ids
+  const int* ket;   // ket list: pair ids of the ket class, Q descending
+  const int* kbeg;  // [nbra] first ket index for each bra
+  const int* kend;  // [nbra] one past the last ket index
+  const int* ioff;  // [nbra+1] first work item of each bra (32 kets per item)
+  int nbra;
+  int nitems;
+  int* counter;     // work-item counter, zero before the launch
+};
+
+// pair class of (la, lb), la >= lb: ss 0, ps 1, pp 2, ds 3, dp 4, dd 5
+__host__ __device__ inline int pair_class(int la, int lb) { return la * (la + 1) / 2 + lb; }
+__host__ __device__ inline int class_index(int la, int lb, int lc, int ld) {
+  const int x = pair_class(la, lb), y = pair_class(lc, ld);
+  return x * (x + 1) / 2 + y;
+}
+
+typedef void (*jk_launch_fn)(const JKWork&, const PairSet&, const KernelCommon&, const MolJK&, const MolJK*, int,
+                             cudaStream_t);
+typedef void (*store_launch_fn)(const JKWork&, const PairSet&, const KernelCommon&, double*, int, int, cudaStream_t);
+typedef void (*schwarz_launch_fn)(const int*, int, const PairSet&, const KernelCommon&, double*, cudaStream_t);
+typedef int (*occ_fn)();
+
+struct EriClassOps {
+  jk_launch_fn jk64;
+  jk_launch_fn jk32;
+  store_launch_fn store;
+  schwarz_launch_fn schwarz;
+  occ_fn occ64;
+  occ_fn occ32;
+  int vrr_flops;  // per primitive quartet, as generated
+  int hrr_flops;  // per contracted quartet
+  const char* name;
+};
+
+#ifndef HF_NCLASS
+#define HF_NCLASS 21
+#endif
+#define HF_NPAIRCLASS 6
+
+// Filled by the per-class translation units.
+void hf_register_classes_sp(EriClassOps* table);
+void hf_register_classes_d1(EriClassOps* table);
+void hf_register_classes_d2(EriClassOps* table);
+void hf_register_classes_d3(EriClassOps* table);
+void hf_register_classes_d4(EriClassOps* table);
+void hf_register_classes_d5(EriClassOps* table);
+void hf_register_classes_d6(EriClassOps* table);

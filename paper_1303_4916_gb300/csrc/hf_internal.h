@@ -1,0 +1,124 @@
+// hf_internal.h -- host-side structures of libhf (not part of the ABI).
+#pragma once
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hf.h"
+#include "hf_device.h"
+
+// ------------------------------------------------------------- errors
+int hf_fail(int code, const char* fmt, ...);  // records the message, returns code
+#define HF_CUDA(call)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return hf_fail(HF_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, \
+                                          cudaGetErrorString(e_));                                 \
+  } while (0)
+#define HF_CHECK(expr)         \
+  do {                         \
+    int rc_ = (expr);          \
+    if (rc_ != HF_OK) return rc_; \
+  } while (0)
+
+// ------------------------------------------------------------- context
+struct hf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cublasHandle_t cublas = nullptr;
+  cusolverDnHandle_t cusolver = nullptr;
+  size_t hbm_budget = 0;
+  int num_sms = 0;
+  double* boys64 = nullptr;
+  float* boys32 = nullptr;
+  EriClassOps ops[HF_NCLASS] = {};
+  std::atomic<int> fail_countdown{0};
+  std::atomic<long long> device_bytes{0};
+  std::mutex mu;  // serialises use of the stream-bound library handles
+};
+
+// Stream-ordered device allocation through the context (honours the
+// fault-injection hook).  Returns HF_OK / HF_ERR_OOM.
+int hf_dev_alloc(hf_ctx* ctx, void** p, size_t bytes);
+void hf_dev_free(hf_ctx* ctx, void* p, size_t bytes);
+
+template <typename T>
+struct DevArray {
+  T* ptr = nullptr;
+  size_t n = 0;
+  hf_ctx* ctx = nullptr;
+  int alloc(hf_ctx* c, size_t count) {
+    release();
+    ctx = c;
+    n = count;
+    if (count == 0) return HF_OK;
+    void* p = nullptr;
+    int rc = hf_dev_alloc(c, &p, count * sizeof(T));
+    if (rc != HF_OK) { n = 0; return rc; }
+    ptr = static_cast<T*>(p);
+    return HF_OK;
+  }
+  void release() {
+    if (ptr) hf_dev_free(ctx, ptr, n * sizeof(T));
+    ptr = nullptr;
+    n = 0;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+  ~DevArray() { release(); }
+};
+
+// ------------------------------------------------------------- basis
+struct ClassWork {
+  DevArray<int> bra, kbeg, kend, ioff;
+  JKWork w{};
+  long long nquartets = 0;
+};
+
+struct hf_basis {
+  hf_ctx* ctx = nullptr;
+  int natom = 0, nshell = 0, nbf = 0, nprim = 0, nelec = 0, lmax = 0;
+  std::vector<hf_atom> atoms;
+  std::vector<int> sh_atom, sh_l, sh_nprim, sh_prim, sh_bf;
+  std::vector<double> exps, coefs;   // coefs: normalised, axial component
+  double e_nuc = 0.0;
+
+  // shell pairs, grouped by pair class, l_A >= l_B
+  int npairs = 0, nprimpairs = 0;
+  std::vector<int> pair_A, pair_B;
+  int class_begin[HF_NPAIRCLASS + 1] = {};
+  DevArray<double> prim64;
+  DevArray<float> prim32;
+  DevArray<PairInfo> pinfo;
+  DevArray<double> Q;                 // per pair
+  std::vector<double> Q_h;
+  std::vector<int> nprim_sig_h;
+  DevArray<int> ketlist;              // per pair class: pair ids sorted by Q descending
+  std::vector<int> ketlist_h;
+
+  // work lists for (tau, fp32_bound)
+  bool have_work = false;
+  double work_tau = -1.0, work_fp32 = -1.0;
+  ClassWork work64[HF_NCLASS], work32[HF_NCLASS];
+  DevArray<int> counters;             // 2 * HF_NCLASS
+
+  // scratch used by host-pointer J/K calls
+  DevArray<double> hD, hJ, hK;
+
+  // one-electron data (lazily)
+  DevArray<double> S, T, V;
+  bool have_one = false;
+};
+
+int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound);
+int hf_basis_one_electron(hf_basis* b);  // fills b->S, T, V
+int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts& o,
+                      long long* nquartets);
+int hf_boys_tables(hf_ctx* ctx);
+int hf_eri_tensor_device(hf_basis* b, double* G);
+int hf_jk_stored_device(hf_basis* b, const double* G, const double* D, double* J, double* K);

@@ -1,0 +1,229 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances (plain FP64): ERIs and one-electron integrals 1e-12 absolute,
+J / K / Fock 1e-10 absolute, SCF energy 1e-8 Eh.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import h_line, lattice_molecule, random_shells_molecule
+
+pytestmark = pytest.mark.gpu
+
+ERI_TOL = 1e-12
+JK_TOL = 1e-10
+E_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def hf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1303_4916_gb300 as hf
+    return hf
+
+
+@pytest.fixture(scope="module")
+def ctx(hf):
+    return hf.Context(0)
+
+
+def _density(n, seed, nocc=None):
+    rng = np.random.default_rng(seed)
+    C = rng.normal(size=(n, nocc or max(1, n // 3))) / np.sqrt(n)
+    return C @ C.T
+
+
+def _t(x):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda:0")
+
+
+SPD_CASES = [((0,), 1), ((1, 0), 2), ((1, 1, 0), 3), ((2, 0), 4), ((2, 1, 0), 5), ((2, 2, 1, 0), 6),
+             ((2, 1, 2, 0, 1), 7)]
+
+
+@pytest.mark.parametrize("ls,seed", SPD_CASES)
+def test_eri_tensor_all_classes(ctx, hf, ls, seed):
+    mol = random_shells_molecule(ls, seed, nprim=(1, 3), exp_range=(0.1, 8.0), box=3.0)
+    ob = oracle.Basis(mol)
+    G0 = ob.eri_tensor()
+    G = hf.Basis(ctx, mol).eri_tensor().cpu().numpy()
+    assert np.abs(G - G0).max() <= ERI_TOL
+
+
+@pytest.mark.parametrize("ls,seed", SPD_CASES[3:])
+def test_one_electron(ctx, hf, ls, seed):
+    Z = np.arange(1, len(ls) + 1, dtype=np.int32) % 9 + 1
+    mol = random_shells_molecule(ls, seed, nprim=(1, 3), exp_range=(0.1, 8.0), box=3.0, Z=Z)
+    S0, T0, V0 = oracle.Basis(mol).one_electron()
+    S, T, V, en = hf.Basis(ctx, mol).one_electron()
+    assert np.abs(S.cpu().numpy() - S0).max() <= ERI_TOL
+    assert np.abs(T.cpu().numpy() - T0).max() <= ERI_TOL
+    assert np.abs(V.cpu().numpy() - V0).max() <= 1e-11
+    assert en == pytest.approx(oracle.Basis(mol).nuclear_repulsion(), abs=1e-12)
+
+
+@pytest.mark.parametrize("ls,seed", SPD_CASES)
+def test_schwarz(ctx, hf, ls, seed):
+    mol = random_shells_molecule(ls, seed, nprim=(1, 3), exp_range=(0.1, 8.0), box=3.0)
+    Q0 = oracle.Basis(mol).schwarz()
+    Q = hf.Basis(ctx, mol).schwarz()
+    np.testing.assert_allclose(Q, Q0, rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("natom,seed,rules", [(3, 1, "sp"), (6, 2, "sp"), (5, 3, "spd"), (9, 4, "s")])
+@pytest.mark.parametrize("tau", [0.0, 1e-12])
+def test_fock_jk_small(ctx, hf, natom, seed, rules, tau):
+    mol = lattice_molecule(natom, seed, rules)
+    ob = oracle.Basis(mol)
+    D = _density(ob.nbf, seed)
+    J0, K0, nq0 = ob.jk(D, tau=tau)
+    basis = hf.Basis(ctx, mol)
+    J, K = basis.fock_jk(_t(D), opts=hf.jk_opts(schwarz_tau=tau))
+    assert np.abs(J.cpu().numpy() - J0).max() <= JK_TOL
+    assert np.abs(K.cpu().numpy() - K0).max() <= JK_TOL
+    nq, _ = basis.count_quartets(hf.jk_opts(schwarz_tau=tau))
+    assert abs(nq - nq0) <= max(2, nq0 // 10000)   # Schwarz ties at the threshold may differ
+
+
+def test_fock_jk_host_pointers_match_device(ctx, hf):
+    mol = lattice_molecule(5, 9, "sp")
+    basis = hf.Basis(ctx, mol)
+    D = _density(basis.nbf, 1)
+    J, K = basis.fock_jk(_t(D))
+    Jh, Kh = basis.fock_jk(D)   # numpy -> HF_JK_HOST path
+    assert np.abs(Jh - J.cpu().numpy()).max() <= 1e-13
+    assert np.abs(Kh - K.cpu().numpy()).max() <= 1e-13
+
+
+def test_fock_jk_ragged_many_tiles(ctx, hf):
+    # enough pairs per class for many 32-ket work items with ragged tails
+    mol = lattice_molecule(14, 21, "sp")
+    ob = oracle.Basis(mol)
+    D = _density(ob.nbf, 5)
+    J0, K0, _ = ob.jk(D, tau=1e-12, nthreads=oracle.oracle_threads())
+    J, K = hf.Basis(ctx, mol).fock_jk(_t(D))
+    assert np.abs(J.cpu().numpy() - J0).max() <= JK_TOL
+    assert np.abs(K.cpu().numpy() - K0).max() <= JK_TOL
+
+
+def test_scf_h_line_stored_and_direct(ctx, hf):
+    mol = h_line()
+    ro = oracle.rhf(mol, max_iter=30, e_tol=1e-8, diis_size=0)
+    basis = hf.Basis(ctx, mol)
+    for stored in (False, True):
+        r = basis.scf(max_iter=30, e_tol=1e-8, diis_size=0, schwarz_tau=0.0, stored_eri=stored)
+        assert r.converged == ro.converged
+        assert abs(r.energy - ro.energy) <= E_TOL
+        assert np.abs(r.tensors["F1"].cpu().numpy() - ro.F1).max() <= JK_TOL
+    G = basis.eri_tensor()
+    D = _t(ro.D)
+    J, K = basis.jk_stored(G, D)
+    J0, K0, _ = oracle.Basis(mol).jk(ro.D)
+    assert np.abs(J.cpu().numpy() - J0).max() <= JK_TOL
+    assert np.abs(K.cpu().numpy() - K0).max() <= JK_TOL
+
+
+@pytest.mark.parametrize("natom,seed,rules", [(4, 31, "sp"), (6, 32, "sp"), (3, 33, "spd")])
+def test_scf_diis_small(ctx, hf, natom, seed, rules):
+    mol = lattice_molecule(natom, seed, rules)
+    ro = oracle.rhf(mol, max_iter=128, e_tol=1e-8, diis_size=8, tau=1e-12)
+    r = hf.Basis(ctx, mol).scf(max_iter=128, e_tol=1e-8, diis_size=8, schwarz_tau=1e-12)
+    assert r.converged == ro.converged
+    assert abs(r.energy - ro.energy) <= E_TOL
+    if ro.homo_lumo_gap > 1e-8:
+        assert np.abs(r.tensors["D"].cpu().numpy() - ro.D).max() <= 1e-6
+    assert np.abs(r.tensors["F1"].cpu().numpy() - ro.F1).max() <= JK_TOL
+
+
+def test_c2_full_size_sampled_rows(ctx, hf):
+    """40-atom s+p lattice (the benchmark workload): J/K rows against the
+    oracle's row-wise definition, in the launch configuration the benchmark
+    times (Schwarz tau 1e-12, FP64)."""
+    mol = lattice_molecule(40, 1, "sp")
+    ob = oracle.Basis(mol)
+    D = _density(ob.nbf, 77, nocc=mol.n_electrons // 2)
+    basis = hf.Basis(ctx, mol)
+    J, K = basis.fock_jk(_t(D))
+    J = J.cpu().numpy()
+    K = K.cpu().numpy()
+    rows = np.array([0, 101, ob.nbf - 1])
+    Jr, Kr = ob.jk_rows(D, rows, tau=1e-12, nthreads=oracle.oracle_threads())
+    assert np.abs(J[rows] - Jr).max() <= JK_TOL
+    assert np.abs(K[rows] - Kr).max() <= JK_TOL
+    assert np.abs(J - J.T).max() == 0.0 and np.abs(K - K.T).max() == 0.0
+
+
+def test_fp32_split_error_is_bounded(ctx, hf):
+    mol = lattice_molecule(12, 41, "sp")
+    ob = oracle.Basis(mol)
+    D = _density(ob.nbf, 9, nocc=mol.n_electrons // 2)
+    J0, K0, _ = ob.jk(D, tau=1e-12, nthreads=oracle.oracle_threads())
+    basis = hf.Basis(ctx, mol)
+    nq, nf = basis.count_quartets(hf.jk_opts(fp32_bound=1e-5))
+    assert 0 < nf < nq
+    for boys32 in (False, True):
+        J, K = basis.fock_jk(_t(D), opts=hf.jk_opts(fp32_bound=1e-5, fp32_boys=boys32))
+        dj = np.abs(J.cpu().numpy() - J0).max()
+        dk = np.abs(K.cpu().numpy() - K0).max()
+        assert dj <= 1e-7 and dk <= 1e-7, (dj, dk)
+
+
+def test_errors(ctx, hf):
+    mol = lattice_molecule(3, 1, "sp")
+    with pytest.raises(hf.HFError) as e:
+        hf.Basis(ctx, mol, n_electrons=3)
+    assert e.value.code == -8
+    bad = mol.copy()
+    bad.shell_l = bad.shell_l.copy()
+    bad.shell_l[0] = 3
+    with pytest.raises(hf.HFError) as e:
+        hf.Basis(ctx, bad)
+    assert e.value.code == -2
+    bad = mol.copy()
+    bad.exps = bad.exps.copy()
+    bad.exps[0] = -1.0
+    with pytest.raises(hf.HFError) as e:
+        hf.Basis(ctx, bad)
+    assert e.value.code == -1
+    # linear dependence: the same shell twice on one atom
+    from synth.molecules import _pack
+    dup = _pack([1, 1], [[0, 0, 0], [1.4, 0, 0]], [(0, 0, [1.0], [1.0]), (0, 0, [1.0], [1.0]), (1, 0, [1.0], [1.0])],
+                "dup", 0, n_electrons=2)
+    r = hf.Basis(ctx, dup)
+    with pytest.raises(hf.HFError) as e:
+        r.scf()
+    assert e.value.code == -4
+
+
+def test_not_converged_reports_partial(ctx, hf):
+    mol = lattice_molecule(4, 31, "sp")
+    r = hf.Basis(ctx, mol).scf(max_iter=1, diis_size=0)
+    assert r.rc == -5 and not r.converged and r.iterations == 1 and np.isfinite(r.energy)
+
+
+def test_injected_allocation_failure(ctx, hf):
+    mol = lattice_molecule(4, 5, "sp")
+    ctx.inject_alloc_failure(3)
+    with pytest.raises(hf.HFError) as e:
+        hf.Basis(ctx, mol)
+    assert e.value.code == -3
+    ctx.inject_alloc_failure(0)
+    hf.Basis(ctx, mol)   # context still usable
+
+
+def test_single_function_and_zero_electrons(ctx, hf):
+    from synth.molecules import _pack
+    m = _pack([2], [[0.0, 0.0, 0.0]], [(0, 0, [0.7671], [1.0])], "he", 0, n_electrons=2)
+    r = hf.Basis(ctx, m).scf(max_iter=5, e_tol=1e-12)
+    a = 0.7671
+    ref = 3 * a - 8 * np.sqrt(2 * a / np.pi) + 2 * np.sqrt(a / np.pi)
+    assert abs(r.energy - ref) <= 1e-12
+    m0 = lattice_molecule(3, 1, "sp")
+    b0 = hf.Basis(ctx, m0, n_electrons=0)
+    D = _density(b0.nbf, 1) * 0.0
+    J, K = b0.fock_jk(_t(D))
+    assert float(J.abs().max()) == 0.0 and float(K.abs().max()) == 0.0
