@@ -208,6 +208,22 @@ int hf_class_stats_get(hf_basis* b, const hf_jk_opts* opts, hf_class_stats* out 
 int hf_fock_jk_profiled(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts* opts,
                         double* class_ms);
 
+/* hf_fock_jk for callers that cannot allocate device memory.  The paper
+ * has no counterpart: it is a deployment form of the J/K build above for
+ * code where cudaMalloc is off limits when the Fock build runs (a frozen
+ * allocator, a host framework that owns all device memory, a real-time
+ * loop).  Same inputs, outputs and results as hf_fock_jk (device pointers
+ * only); the J'/K' accumulators and work-item counters live in one static
+ * device array of the library, so the call allocates nothing.
+ * Limits: nbf <= 512 (HF_ERR_TOO_LARGE above); about 4 MiB of static device
+ * memory is held on every GPU that loads the library until exit.
+ * The first call on a device looks up the array's address (once per
+ * device): make it before any stream capture.  All calls share the array,
+ * so calls that overlap on the GPU race.  The quartet work lists for the
+ * options must already exist on the basis (a prior hf_fock_jk or
+ * hf_count_quartets with the same options), else HF_ERR_INVALID. */
+int hf_fock_jk_noalloc(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts* opts);
+
 /* One-electron matrices of Eqs. 2-4 (device pointers, any may be NULL)
  * and the nuclear repulsion energy (host, may be NULL). */
 int hf_one_electron(hf_basis* b, double* S, double* T, double* V, double* e_nuc);

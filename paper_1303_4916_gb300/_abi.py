@@ -113,6 +113,7 @@ SIGNATURES = {
     "hf_fock_jk": (I, [P, P, P, P, C.POINTER(hf_jk_opts)]),
     "hf_class_stats_get": (I, [P, C.POINTER(hf_jk_opts), C.POINTER(hf_class_stats)]),
     "hf_fock_jk_profiled": (I, [P, P, P, P, C.POINTER(hf_jk_opts), C.POINTER(C.c_double)]),
+    "hf_fock_jk_noalloc": (I, [P, P, P, P, C.POINTER(hf_jk_opts)]),
     "hf_one_electron": (I, [P, P, P, P, C.POINTER(D)]),
     "hf_eri_tensor": (I, [P, P]),
     "hf_jk_stored": (I, [P, P, P, P, P]),

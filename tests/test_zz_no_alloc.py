@@ -1,0 +1,74 @@
+"""hf_fock_jk_noalloc: the J/K build for callers that cannot allocate device
+memory (a frozen allocator, a framework that owns all device memory, a
+real-time loop).  It keeps its scratch in a static device array of the
+library, so its results must equal those of hf_fock_jk, call after call,
+even though every call reuses the same scratch.
+
+Collected last (file name) so that a run stopping at the first failure has
+run every other test first; it also passes alone in a fresh process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+JK_TOL = 1e-10   # the tolerance the J/K parity tests use
+
+
+@pytest.fixture(scope="module")
+def hf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1303_4916_gb300 as hf
+    return hf
+
+
+def _density(n, seed, nocc):
+    rng = np.random.default_rng(seed)
+    C = rng.normal(size=(n, nocc)) / np.sqrt(n)
+    return C @ C.T
+
+
+@pytest.mark.parametrize("natom,seed,rules", [(8, 12, "sp"), (5, 3, "spd")])
+def test_noalloc_matches_fock_jk_on_two_calls(hf, natom, seed, rules):
+    import torch
+    from synth import lattice_molecule
+    lib = hf.load()
+    ctx = hf.Context(0)
+    basis = hf.Basis(ctx, lattice_molecule(natom, seed, rules))
+    n = basis.nbf
+    opts = hf.jk_opts()
+    D = torch.tensor(_density(n, seed, max(1, basis.n_electrons // 2)), dtype=torch.float64, device="cuda:0")
+    J0, K0 = basis.fock_jk(D, opts=opts)          # reference; also builds the work lists
+    for call in range(2):
+        J = torch.full_like(D, float("nan"))
+        K = torch.full_like(D, float("nan"))
+        rc = lib.hf_fock_jk_noalloc(basis.handle, D.data_ptr(), J.data_ptr(), K.data_ptr(), ctypes.byref(opts))
+        assert rc == 0, lib.hf_last_error()
+        torch.cuda.synchronize()
+        assert float((J - J0).abs().max()) <= JK_TOL, call
+        assert float((K - K0).abs().max()) <= JK_TOL, call
+        D = D * 0.5                                # second call: different density, same scratch
+        J0, K0 = basis.fock_jk(D, opts=opts)
+
+
+def test_noalloc_rejects_what_it_cannot_serve(hf):
+    import torch
+    from synth import lattice_molecule
+    lib = hf.load()
+    ctx = hf.Context(0)
+    small = hf.Basis(ctx, lattice_molecule(3, 1, "sp"))
+    D = torch.zeros((small.nbf, small.nbf), dtype=torch.float64, device="cuda:0")
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    other = hf.jk_opts(schwarz_tau=1e-9)         # no work lists prepared for these options
+    rc = lib.hf_fock_jk_noalloc(small.handle, D.data_ptr(), J.data_ptr(), K.data_ptr(), ctypes.byref(other))
+    assert rc == -1 and b"work lists" in lib.hf_last_error()
+    big = hf.Basis(ctx, lattice_molecule(110, 2, "sp"))   # nbf > 512
+    assert big.nbf > 512
+    Db = torch.zeros((big.nbf, big.nbf), dtype=torch.float64, device="cuda:0")
+    rc = lib.hf_fock_jk_noalloc(big.handle, Db.data_ptr(), Db.data_ptr(), Db.data_ptr(), None)
+    assert rc == -12 and b"512" in lib.hf_last_error()
