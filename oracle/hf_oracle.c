@@ -685,7 +685,9 @@ long or_jk(const or_basis *B, const double *P, double *J, double *K, double tau,
  * J_ij = sum_kl (ij|kl) P_kl and K_il = sum_jk (ij|kl) P_jk for each i in
  * rows[0..nrows), all j (resp. l).  Jrows/Krows are nrows x nbf.  Every
  * shell quartet (I J|K L) with I the shell of row i is evaluated (no
- * permutational symmetry); tau > 0 applies the Schwarz rule. */
+ * permutational symmetry), except those whose terms are all zero because
+ * both density blocks they meet, P[K,L] and P[J,K], are zero; tau > 0
+ * applies the Schwarz rule. */
 void or_jk_rows(const or_basis *B, const double *P, int nrows, const int *rows,
                 double *Jrows, double *Krows, double tau, int nthreads)
 {
@@ -695,6 +697,13 @@ void or_jk_rows(const or_basis *B, const double *P, int nrows, const int *rows,
         Q = (double *)malloc(sizeof(double) * ns * ns);
         or_schwarz(B, Q);
     }
+    /* nz[X*ns+Y]: the density block of shells X, Y has a nonzero entry */
+    char *nz = (char *)calloc((size_t)ns * ns, 1);
+    for (int X = 0; X < ns; ++X)
+        for (int Y = 0; Y < ns; ++Y)
+            for (int x = B->sh_bf[X]; x < B->sh_bf[X + 1] && !nz[X * ns + Y]; ++x)
+                for (int y = B->sh_bf[Y]; y < B->sh_bf[Y + 1]; ++y)
+                    if (P[x * n + y] != 0.0) { nz[X * ns + Y] = 1; break; }
     memset(Jrows, 0, sizeof(double) * nrows * n);
     memset(Krows, 0, sizeof(double) * nrows * n);
     if (nthreads < 1) nthreads = 1;
@@ -713,6 +722,7 @@ void or_jk_rows(const or_basis *B, const double *P, int nrows, const int *rows,
             for (int Js = 0; Js < ns; ++Js)
                 for (int Ks = 0; Ks < ns; ++Ks)
                     for (int Ls = 0; Ls < ns; ++Ls) {
+                        if (!nz[Ks * ns + Ls] && !nz[Js * ns + Ks]) continue;
                         if (Q && Q[I * ns + Js] * Q[Ks * ns + Ls] < tau) continue;
                         eri_block(ws, B, I, Js, Ks, Ls, blk);
                         int nb = OR_NCART(B->sh_l[Js]), nc = OR_NCART(B->sh_l[Ks]), nd = OR_NCART(B->sh_l[Ls]);
@@ -739,6 +749,7 @@ void or_jk_rows(const or_basis *B, const double *P, int nrows, const int *rows,
             free(Kt);
         }
     }
+    free(nz);
     free(Q);
 }
 

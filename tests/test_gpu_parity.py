@@ -74,7 +74,7 @@ def test_schwarz(ctx, hf, ls, seed):
     np.testing.assert_allclose(Q, Q0, rtol=1e-11, atol=1e-14)
 
 
-@pytest.mark.parametrize("natom,seed,rules", [(3, 1, "sp"), (6, 2, "sp"), (5, 3, "spd"), (9, 4, "s")])
+@pytest.mark.parametrize("natom,seed,rules", [(3, 1, "sp"), (6, 2, "sp"), (3, 3, "spd"), (9, 4, "s")])
 @pytest.mark.parametrize("tau", [0.0, 1e-12])
 def test_fock_jk_small(ctx, hf, natom, seed, rules, tau):
     mol = lattice_molecule(natom, seed, rules)
@@ -101,7 +101,7 @@ def test_fock_jk_host_pointers_match_device(ctx, hf):
 
 def test_fock_jk_ragged_many_tiles(ctx, hf):
     # enough pairs per class for many 32-ket work items with ragged tails
-    mol = lattice_molecule(14, 21, "sp")
+    mol = lattice_molecule(10, 21, "sp")
     ob = oracle.Basis(mol)
     D = _density(ob.nbf, 5)
     J0, K0, _ = ob.jk(D, tau=1e-12, nthreads=oracle.oracle_threads())
@@ -130,7 +130,7 @@ def test_scf_h_line_stored_and_direct(ctx, hf):
 @pytest.mark.parametrize("natom,seed,rules", [(4, 31, "sp"), (6, 32, "sp"), (3, 33, "spd")])
 def test_scf_diis_small(ctx, hf, natom, seed, rules):
     mol = lattice_molecule(natom, seed, rules)
-    ro = oracle.rhf(mol, max_iter=128, e_tol=1e-8, diis_size=8, tau=1e-12)
+    ro = oracle.rhf(mol, max_iter=128, e_tol=1e-8, diis_size=8, tau=1e-12, nthreads=oracle.oracle_threads())
     r = hf.Basis(ctx, mol).scf(max_iter=128, e_tol=1e-8, diis_size=8, schwarz_tau=1e-12)
     assert r.converged == ro.converged
     assert abs(r.energy - ro.energy) <= E_TOL
@@ -142,23 +142,31 @@ def test_scf_diis_small(ctx, hf, natom, seed, rules):
 def test_c2_full_size_sampled_rows(ctx, hf):
     """40-atom s+p lattice (the benchmark workload): J/K rows against the
     oracle's row-wise definition, in the launch configuration the benchmark
-    times (Schwarz tau 1e-12, FP64)."""
+    times (Schwarz tau 1e-12, FP64).  The density is supported on a random
+    subset of 16 shells so that the oracle's rows stay cheap; the GPU still
+    evaluates every surviving quartet."""
     mol = lattice_molecule(40, 1, "sp")
     ob = oracle.Basis(mol)
-    D = _density(ob.nbf, 77, nocc=mol.n_electrons // 2)
+    rng = np.random.default_rng(78)
+    shells = np.sort(rng.choice(mol.nshell, size=16, replace=False))
+    idx = np.concatenate([np.arange(ob.shell_bf[s], ob.shell_bf[s + 1]) for s in shells])
+    C = np.zeros((ob.nbf, 8))
+    C[idx] = rng.normal(size=(idx.size, 8)) / np.sqrt(idx.size)
+    D = C @ C.T
     basis = hf.Basis(ctx, mol)
     J, K = basis.fock_jk(_t(D))
     J = J.cpu().numpy()
     K = K.cpu().numpy()
-    rows = np.array([0, 101, ob.nbf - 1])
+    rows = np.array([0, 57, 101, int(idx[3]), ob.nbf - 1])
     Jr, Kr = ob.jk_rows(D, rows, tau=1e-12, nthreads=oracle.oracle_threads())
     assert np.abs(J[rows] - Jr).max() <= JK_TOL
     assert np.abs(K[rows] - Kr).max() <= JK_TOL
     assert np.abs(J - J.T).max() == 0.0 and np.abs(K - K.T).max() == 0.0
+    assert np.abs(Kr).max() > 1e-3 and np.abs(Jr).max() > 1e-3
 
 
 def test_fp32_split_error_is_bounded(ctx, hf):
-    mol = lattice_molecule(12, 41, "sp")
+    mol = lattice_molecule(9, 41, "sp")
     ob = oracle.Basis(mol)
     D = _density(ob.nbf, 9, nocc=mol.n_electrons // 2)
     J0, K0, _ = ob.jk(D, tau=1e-12, nthreads=oracle.oracle_threads())

@@ -311,3 +311,19 @@ def test_scf_h_line_no_diis():
     assert r.energy < 0
     # variational: the SCF energy is not above the core-guess energy of D_1
     assert r.energy <= r.energies[0] + 1e-12
+
+
+def test_jk_rows_with_zero_density_blocks():
+    # rows skip quartets whose density blocks are zero: same result as the full build
+    mol = _small_spd(9)
+    B = oracle.Basis(mol)
+    D = _rand_density(B.nbf, 8)
+    keep = np.zeros(B.nbf, dtype=bool)
+    for s in (0, 3):
+        keep[B.shell_bf[s]:B.shell_bf[s + 1]] = True
+    D = D * np.outer(keep, keep)
+    J, K, _ = B.jk(D)
+    rows = np.arange(B.nbf)
+    Jr, Kr = B.jk_rows(D, rows)
+    np.testing.assert_allclose(Jr, J, atol=1e-13, rtol=0)
+    np.testing.assert_allclose(Kr, K, atol=1e-13, rtol=0)
