@@ -91,7 +91,7 @@ __global__ void pair_kernel(int npairs, const int* __restrict__ pA, const int* _
   pi.nprim = nsig;
   pi.AB[0] = ABx; pi.AB[1] = ABy; pi.AB[2] = ABz;
   pi.same = (A == B);
-  pi.mol = 0;
+  pi.pad = 0;
   info[t] = pi;
 }
 
@@ -305,13 +305,23 @@ extern "C" int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, con
     }
     b->nprim_sig_h.resize(np);
     for (int k = 0; k < np; ++k) b->nprim_sig_h[k] = info_h[k].nprim;
-    // Ket lists: pairs of each class sorted by Q descending.
+    // Ket lists: the pairs of each class in buckets of equal significant
+    // primitive-pair count (descending), Q descending inside a bucket, so
+    // the 32 lanes of a warp loop over the same number of primitives and
+    // the Schwarz-surviving kets of a bucket are a prefix of it.
     b->ketlist_h.resize(np);
     for (int X = 0; X < HF_NPAIRCLASS; ++X) {
       const int s0 = b->class_begin[X], s1 = b->class_begin[X + 1];
       for (int k = s0; k < s1; ++k) b->ketlist_h[k] = k;
-      std::stable_sort(b->ketlist_h.begin() + s0, b->ketlist_h.begin() + s1,
-                       [&](int x, int y) { return b->Q_h[x] > b->Q_h[y]; });
+      std::stable_sort(b->ketlist_h.begin() + s0, b->ketlist_h.begin() + s1, [&](int x, int y) {
+        if (b->nprim_sig_h[x] != b->nprim_sig_h[y]) return b->nprim_sig_h[x] > b->nprim_sig_h[y];
+        return b->Q_h[x] > b->Q_h[y];
+      });
+      b->buckets[X].clear();
+      for (int k = s0; k < s1; ++k)
+        if (k == s0 || b->nprim_sig_h[b->ketlist_h[k]] != b->nprim_sig_h[b->ketlist_h[k - 1]])
+          b->buckets[X].push_back(k - s0);
+      b->buckets[X].push_back(s1 - s0);
     }
     if (cudaMemcpyAsync(b->ketlist.ptr, b->ketlist_h.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st) !=
         cudaSuccess) {
@@ -362,12 +372,13 @@ extern "C" int hf_schwarz(hf_basis* b, double* Q) {
 }
 
 // ------------------------------------------------------------- work lists
-// For each canonical class (X|Y), X >= Y: bra entries are the pairs of
-// class X in Q-descending order; for bra i the kept kets are the prefix of
-// the class-Y list with Q_i Q_k >= tau (the Schwarz rule: drop iff
-// Q_ab Q_cd < tau), cut at k <= i when X == Y so each unordered pair of
-// pairs appears once.  The kets with Q_i Q_k >= fp32_bound form the FP64
-// range, the rest the FP32 range.
+// For each canonical class (X|Y), X >= Y: every pair of class X is a bra;
+// its kets are taken bucket by bucket from the class-Y list.  Inside a
+// bucket (Q descending) the kept kets are the prefix with Q_i Q_k >= tau
+// (the Schwarz rule: drop iff Q_ab Q_cd < tau); when X == Y only kets at
+// list positions <= the bra's own position are taken, so each unordered
+// pair of pairs appears once.  Kets with Q_i Q_k >= fp32_bound form the
+// FP64 range of the entry, the rest its FP32 range.
 int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
   if (b->have_work && b->work_tau == tau && b->work_fp32 == fp32_bound) return HF_OK;
   hf_ctx* ctx = b->ctx;
@@ -376,8 +387,8 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
     for (int Y = 0; Y <= X; ++Y) {
       const int cls = X * (X + 1) / 2 + Y;
       const int xb = b->class_begin[X], xe = b->class_begin[X + 1];
-      const int yb = b->class_begin[Y], ye = b->class_begin[Y + 1];
-      const int ny = ye - yb;
+      const int yb = b->class_begin[Y];
+      const std::vector<int>& bk = b->buckets[Y];
       std::vector<int> bra[2], kb[2], ke[2], io[2];
       long long nq[2] = {0, 0};
       io[0].push_back(0);
@@ -385,32 +396,37 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
       for (int i = xb; i < xe; ++i) {
         const int pi = b->ketlist_h[i];
         const double qi = b->Q_h[pi];
-        // first k with qi * Q_k < tau (Q descending => monotone)
-        auto count_ge = [&](double thr) {
-          int lo = 0, hi = ny;
-          while (lo < hi) {
-            const int mid = (lo + hi) / 2;
-            if (qi * b->Q_h[b->ketlist_h[yb + mid]] >= thr) lo = mid + 1; else hi = mid;
+        const int ipos = i - xb;  // the bra's position in the class-X list (== class-Y list when X == Y)
+        for (size_t u = 0; u + 1 < bk.size(); ++u) {
+          const int b0 = bk[u], b1 = bk[u + 1];
+          if (X == Y && b0 > ipos) break;
+          auto count_ge = [&](double thr) {  // first position in [b0, b1) with qi * Q < thr
+            int lo = b0, hi = b1;
+            while (lo < hi) {
+              const int mid = (lo + hi) / 2;
+              if (qi * b->Q_h[b->ketlist_h[yb + mid]] >= thr) lo = mid + 1; else hi = mid;
+            }
+            return lo;
+          };
+          int n = count_ge(tau);
+          if (X == Y) n = std::min(n, ipos + 1);
+          const int m = fp32_bound > 0.0 ? std::min(count_ge(fp32_bound), n) : n;
+          const int lo_[2] = {b0, m}, hi_[2] = {m, n};
+          for (int r = 0; r < 2; ++r) {
+            const int cnt = hi_[r] - lo_[r];
+            if (cnt <= 0) continue;
+            bra[r].push_back(pi);
+            kb[r].push_back(lo_[r]);
+            ke[r].push_back(hi_[r]);
+            io[r].push_back(io[r].back() + (cnt + 31) / 32);
+            nq[r] += cnt;
           }
-          return lo;
-        };
-        int n = count_ge(tau);
-        if (X == Y) n = std::min(n, i - xb + 1);
-        int m = fp32_bound > 0.0 ? std::min(count_ge(fp32_bound), n) : n;
-        const int lo_[2] = {0, m}, hi_[2] = {m, n};
-        for (int r = 0; r < 2; ++r) {
-          const int cnt = hi_[r] - lo_[r];
-          if (cnt <= 0) continue;
-          bra[r].push_back(pi);
-          kb[r].push_back(lo_[r]);
-          ke[r].push_back(hi_[r]);
-          io[r].push_back(io[r].back() + (cnt + 31) / 32);
-          nq[r] += cnt;
         }
       }
       for (int r = 0; r < 2; ++r) {
         ClassWork& w = r == 0 ? b->work64[cls] : b->work32[cls];
         const int nb = (int)bra[r].size();
+        if (io[r].back() > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "class %d: too many work items", cls);
         HF_CHECK(w.bra.alloc(ctx, nb));
         HF_CHECK(w.kbeg.alloc(ctx, nb));
         HF_CHECK(w.kend.alloc(ctx, nb));
@@ -421,19 +437,22 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
           HF_CUDA(cudaMemcpyAsync(w.kend.ptr, ke[r].data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
           HF_CUDA(cudaMemcpyAsync(w.ioff.ptr, io[r].data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
         }
-        if (io[r].back() > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "class %d: too many work items", cls);
         w.w.bra = w.bra.ptr;
         w.w.ket = b->ketlist.ptr + yb;
         w.w.kbeg = w.kbeg.ptr;
         w.w.kend = w.kend.ptr;
         w.w.ioff = w.ioff.ptr;
+        w.w.mol = nullptr;
         w.w.nbra = nb;
         w.w.nitems = io[r].back();
         w.w.counter = b->counters.ptr + 2 * cls + r;
         w.nquartets = nq[r];
+        w.bra_h = std::move(bra[r]);
+        w.kbeg_h = std::move(kb[r]);
+        w.kend_h = std::move(ke[r]);
       }
     }
-  // host vectors die at return: make sure the uploads have completed
+  // the host vectors above are consumed by the async copies: wait for them
   HF_CUDA(cudaStreamSynchronize(st));
   b->have_work = true;
   b->work_tau = tau;
@@ -530,13 +549,10 @@ extern "C" int hf_class_stats_get(hf_basis* b, const hf_jk_opts* opts, hf_class_
       const int yb = b->class_begin[Y];
       for (int r = 0; r < 2; ++r) {
         ClassWork& w = r == 0 ? b->work64[c] : b->work32[c];
-        std::vector<int> bra(w.w.nbra), kb(w.w.nbra), ke(w.w.nbra);
+        const std::vector<int>& bra = w.bra_h;
+        const std::vector<int>& kb = w.kbeg_h;
+        const std::vector<int>& ke = w.kend_h;
         long long pq = 0;
-        if (w.w.nbra > 0) {
-          HF_CUDA(cudaMemcpy(bra.data(), w.bra.ptr, sizeof(int) * w.w.nbra, cudaMemcpyDeviceToHost));
-          HF_CUDA(cudaMemcpy(kb.data(), w.kbeg.ptr, sizeof(int) * w.w.nbra, cudaMemcpyDeviceToHost));
-          HF_CUDA(cudaMemcpy(ke.data(), w.kend.ptr, sizeof(int) * w.w.nbra, cudaMemcpyDeviceToHost));
-        }
         for (int i = 0; i < w.w.nbra; ++i)
           pq += (long long)b->nprim_sig_h[bra[i]] * (pre[yb + ke[i]] - pre[yb + kb[i]]);
         if (r == 0) { st.quartets_fp64 = w.nquartets; st.prim_quartets_fp64 = pq; }

@@ -222,8 +222,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // ------------------------------------------------------------- J/K kernel
 // items: work item t covers bra list entry bi (found by binary search in
 // ioff) and kets kbeg[bi] + 32*(t - ioff[bi]) + lane of the ket list.
-// one: D/J/K of a single molecule; mols (if not null): per-molecule table
-// indexed by PairInfo::mol for a multi-molecule arena.
+// one: D/J/K of a single molecule (pair data ps, ket list w.ket); mols (if
+// not null): per-molecule table indexed by w.mol[entry], each molecule with
+// its own pair data, ket lists and D/J/K.
 template <class C, typename R>
 __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairSet ps, const KernelCommon kc,
                                                      const MolJK one, const MolJK* __restrict__ mols) {
@@ -240,26 +241,29 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
       if (__ldg(w.ioff + mid) <= t) lo = mid; else hi = mid;
     }
     const int bi = lo;
+    const MolJK* mjp = mols ? mols + __ldg(w.mol + bi) : nullptr;
+    if (mjp && !mjp->active) continue;  // warp-uniform: the entry is shared by the warp
+    const PairSet P = mjp ? mjp->ps : ps;
+    const int* ketb = mjp ? mjp->ketlist + mjp->ket_off[pair_class(C::LC, C::LD)] : w.ket;
     const int bp = __ldg(w.bra + bi);
     const int kidx = __ldg(w.kbeg + bi) + 32 * (t - __ldg(w.ioff + bi)) + lane;
     const bool active = kidx < __ldg(w.kend + bi);
-    const int kp = active ? __ldg(w.ket + kidx) : bp;
-    const PairInfo bra = ps.info[bp];
-    const PairInfo ket = ps.info[kp];
+    const int kp = active ? __ldg(ketb + kidx) : bp;
+    const PairInfo bra = P.info[bp];
+    const PairInfo ket = P.info[kp];
 
     R acc[C::NE * C::NF];
-    contracted_vrr<C, R>(ps, kc, bra.prim0, bra.nprim, ket.prim0, active ? ket.nprim : 0, acc);
+    contracted_vrr<C, R>(P, kc, bra.prim0, bra.nprim, ket.prim0, active ? ket.nprim : 0, acc);
     R I[NA * NB * NC * ND];
     {
       R AB[3] = {(R)bra.AB[0], (R)bra.AB[1], (R)bra.AB[2]};
       R CD[3] = {(R)ket.AB[0], (R)ket.AB[1], (R)ket.AB[2]};
       C::template hrr<R>(acc, I, AB, CD);
     }
-    const MolJK mj = mols ? mols[bra.mol] : one;
-    const double* __restrict__ D = mj.D;
-    double* __restrict__ J = mj.J;
-    double* __restrict__ Kx = mj.K;
-    const int nbf = mj.nbf;
+    const double* __restrict__ D = mjp ? mjp->D : one.D;
+    double* __restrict__ J = mjp ? mjp->J : one.J;
+    double* __restrict__ Kx = mjp ? mjp->K : one.K;
+    const int nbf = mjp ? mjp->nbf : one.nbf;
     double wdeg = active ? 1.0 : 0.0;
     if (bra.same) wdeg *= 0.5;
     if (ket.same) wdeg *= 0.5;

@@ -22,21 +22,11 @@
 
 // Shell pair (A, B) with l_A >= l_B: first basis functions of A and B,
 // offset and count of its significant primitive pairs (sorted by
-// magnitude), AB = A - B, same = (A == B), mol = molecule of the pair in a
-// multi-molecule arena (0 for a single basis).
+// magnitude), AB = A - B, same = (A == B).
 struct PairInfo {
   int bfA, bfB, prim0, nprim;
   double AB[3];
-  int same, mol;
-};
-
-// Density and J/K outputs of one molecule (device, nbf x nbf row-major).
-struct MolJK {
-  const double* D;
-  double* J;
-  double* K;
-  int nbf;
-  int pad;
+  int same, pad;
 };
 
 struct PairSet {
@@ -45,19 +35,39 @@ struct PairSet {
   const PairInfo* info;
 };
 
+#define HF_NPAIRCLASS 6
+
+// One molecule of a launch: density and J/K outputs (device, nbf x nbf
+// row-major), its own pair data and ket lists (ket_off[Y] = start of pair
+// class Y in ketlist), and whether it takes part (inactive molecules'
+// work items are skipped).
+struct MolJK {
+  const double* D;
+  double* J;
+  double* K;
+  int nbf;
+  int active;
+  PairSet ps;
+  const int* ketlist;
+  int ket_off[HF_NPAIRCLASS];
+};
+
 struct KernelCommon {
   const double* boys64;
   const float* boys32;
   int boys_fp32;  // evaluate F_m in FP32 for reduced-precision quartets
 };
 
-// Work list of one (class, precision) launch.
+// Work list of one (class, precision) launch.  Entry e pairs bra pair
+// bra[e] with the kets ket[kbeg[e] .. kend[e]) of the ket class list
+// (significant-primitive-count buckets, Schwarz-descending inside each).
 struct JKWork {
   const int* bra;   // [nbra] bra pair ids
-  const int* ket;   // ket list: pair ids of the ket class, Q descending
-  const int* kbeg;  // [nbra] first ket index for each bra
+  const int* ket;   // ket list of the ket class (single-molecule launches)
+  const int* kbeg;  // [nbra] first ket index of each entry
   const int* kend;  // [nbra] one past the last ket index
-  const int* ioff;  // [nbra+1] first work item of each bra (32 kets per item)
+  const int* ioff;  // [nbra+1] first work item of each entry (32 kets per item)
+  const int* mol;   // [nbra] molecule of each entry (multi-molecule launches), else null
   int nbra;
   int nitems;
   int* counter;     // work-item counter, zero before the launch
@@ -91,7 +101,6 @@ struct EriClassOps {
 #ifndef HF_NCLASS
 #define HF_NCLASS 21
 #endif
-#define HF_NPAIRCLASS 6
 
 // Filled by the per-class translation units.
 void hf_register_classes_sp(EriClassOps* table);

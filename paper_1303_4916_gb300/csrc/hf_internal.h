@@ -76,6 +76,7 @@ struct DevArray {
 // ------------------------------------------------------------- basis
 struct ClassWork {
   DevArray<int> bra, kbeg, kend, ioff;
+  std::vector<int> bra_h, kbeg_h, kend_h;  // host copies (multi-molecule launches, statistics)
   JKWork w{};
   long long nquartets = 0;
 };
@@ -98,8 +99,9 @@ struct hf_basis {
   DevArray<double> Q;                 // per pair
   std::vector<double> Q_h;
   std::vector<int> nprim_sig_h;
-  DevArray<int> ketlist;              // per pair class: pair ids sorted by Q descending
+  DevArray<int> ketlist;              // per pair class: pair ids, primitive-count buckets, Q descending
   std::vector<int> ketlist_h;
+  std::vector<int> buckets[HF_NPAIRCLASS];  // bucket boundaries (positions in the class list)
 
   // work lists for (tau, fp32_bound)
   bool have_work = false;

@@ -1,0 +1,226 @@
+// multi.cu -- multi-molecule J/K launches (batched SCF and serving).
+#include <algorithm>
+
+#include "multi.h"
+
+namespace {
+
+// Zero J and K of every active molecule: blockIdx.y = molecule.
+__global__ void zero_jk_batch(const MolJK* __restrict__ mols) {
+  const MolJK m = mols[blockIdx.y];
+  if (!m.active) return;
+  const size_t nn = (size_t)m.nbf * m.nbf;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
+    m.J[t] = 0.0;
+    m.K[t] = 0.0;
+  }
+}
+
+// J = 2 (J' + J'^T), K = K' + K'^T in place for every active molecule.
+__global__ void symmetrize_jk_batch(const MolJK* __restrict__ mols) {
+  const MolJK m = mols[blockIdx.y];
+  if (!m.active) return;
+  const int n = m.nbf;
+  const size_t nn = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (j < i) continue;
+    const size_t ij = (size_t)i * n + j, ji = (size_t)j * n + i;
+    const double sj = 2.0 * (m.J[ij] + m.J[ji]);
+    m.J[ij] = sj;
+    m.J[ji] = sj;
+    const double sk = m.K[ij] + m.K[ji];
+    m.K[ij] = sk;
+    m.K[ji] = sk;
+  }
+}
+
+}  // namespace
+
+int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vector<const double*>& D,
+                   const std::vector<double*>& J, const std::vector<double*>& K) {
+  ctx = c;
+  nmol = (int)mols.size();
+  cudaStream_t st = ctx->stream;
+  table_h.assign(nmol, MolJK{});
+  mol_quartets.assign(nmol, 0);
+  for (int m = 0; m < nmol; ++m) {
+    hf_basis* b = mols[m];
+    MolJK& t = table_h[m];
+    t.D = D[m];
+    t.J = J[m];
+    t.K = K[m];
+    t.nbf = b->nbf;
+    t.active = 1;
+    t.ps = PairSet{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
+    t.ketlist = b->ketlist.ptr;
+    for (int y = 0; y < HF_NPAIRCLASS; ++y) t.ket_off[y] = b->class_begin[y];
+  }
+  HF_CHECK(table.alloc(ctx, std::max(nmol, 1)));
+  if (nmol > 0)
+    HF_CUDA(cudaMemcpyAsync(table.ptr, table_h.data(), sizeof(MolJK) * nmol, cudaMemcpyHostToDevice, st));
+  HF_CHECK(counters.alloc(ctx, 2 * HF_NCLASS));
+  std::vector<int> hb, hkb, hke, hio, hm;
+  for (int c2 = 0; c2 < 2 * HF_NCLASS; ++c2) {
+    const int cls = c2 / 2, r = c2 % 2;
+    hb.clear(); hkb.clear(); hke.clear(); hm.clear(); hio.assign(1, 0);
+    long long nq = 0;
+    for (int m = 0; m < nmol; ++m) {
+      const ClassWork& cw = r == 0 ? mols[m]->work64[cls] : mols[m]->work32[cls];
+      for (size_t e = 0; e < cw.bra_h.size(); ++e) {
+        const int cnt = cw.kend_h[e] - cw.kbeg_h[e];
+        hb.push_back(cw.bra_h[e]);
+        hkb.push_back(cw.kbeg_h[e]);
+        hke.push_back(cw.kend_h[e]);
+        hm.push_back(m);
+        hio.push_back(hio.back() + (cnt + 31) / 32);
+        nq += cnt;
+        mol_quartets[m] += cnt;
+      }
+    }
+    if (hio.back() > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "batched class %d: too many work items", cls);
+    const int nb = (int)hb.size();
+    HF_CHECK(bra[c2].alloc(ctx, nb));
+    HF_CHECK(kbeg[c2].alloc(ctx, nb));
+    HF_CHECK(kend[c2].alloc(ctx, nb));
+    HF_CHECK(mol[c2].alloc(ctx, nb));
+    HF_CHECK(ioff[c2].alloc(ctx, nb + 1));
+    if (nb > 0) {
+      HF_CUDA(cudaMemcpyAsync(bra[c2].ptr, hb.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+      HF_CUDA(cudaMemcpyAsync(kbeg[c2].ptr, hkb.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+      HF_CUDA(cudaMemcpyAsync(kend[c2].ptr, hke.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+      HF_CUDA(cudaMemcpyAsync(mol[c2].ptr, hm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+      HF_CUDA(cudaMemcpyAsync(ioff[c2].ptr, hio.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
+    }
+    JKWork& wk = w[c2];
+    wk.bra = bra[c2].ptr;
+    wk.ket = nullptr;
+    wk.kbeg = kbeg[c2].ptr;
+    wk.kend = kend[c2].ptr;
+    wk.ioff = ioff[c2].ptr;
+    wk.mol = mol[c2].ptr;
+    wk.nbra = nb;
+    wk.nitems = hio.back();
+    wk.counter = counters.ptr + c2;
+    nquartets[c2] = nq;
+    // the host vectors are reused for the next class: let the copies finish
+    HF_CUDA(cudaStreamSynchronize(st));
+  }
+  return HF_OK;
+}
+
+int MultiJK::set_active(const std::vector<int>& active) {
+  for (int m = 0; m < nmol; ++m) table_h[m].active = active[m];
+  if (nmol > 0) {
+    HF_CUDA(cudaMemcpyAsync(table.ptr, table_h.data(), sizeof(MolJK) * nmol, cudaMemcpyHostToDevice, ctx->stream));
+    HF_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  return HF_OK;
+}
+
+int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
+  cudaStream_t st = ctx->stream;
+  if (nmol == 0) return HF_OK;
+  const dim3 g(std::max(1, 2 * ctx->num_sms / std::max(1, nmol)), nmol);
+  zero_jk_batch<<<g, 256, 0, st>>>(table.ptr);
+  HF_CUDA(cudaMemsetAsync(counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
+  const PairSet none{nullptr, nullptr, nullptr};
+  const MolJK one{};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (class_ms) {
+    HF_CUDA(cudaEventCreate(&ev[0]));
+    HF_CUDA(cudaEventCreate(&ev[1]));
+  }
+  for (int cls = HF_NCLASS - 1; cls >= 0; --cls) {
+    const EriClassOps& op = ctx->ops[cls];
+    if (class_ms) HF_CUDA(cudaEventRecord(ev[0], st));
+    bool any = false;
+    for (int r = 0; r < 2; ++r) {
+      const JKWork& wk = w[2 * cls + r];
+      if (wk.nitems <= 0) continue;
+      any = true;
+      const int occ = std::max(r == 0 ? op.occ64() : op.occ32(), 1);
+      const int per_sm = grid_scale[cls] > 0 ? std::min(occ, grid_scale[cls]) : occ;
+      const int grid = std::max(1, std::min((wk.nitems + 3) / 4, per_sm * ctx->num_sms));
+      (r == 0 ? op.jk64 : op.jk32)(wk, none, kc, one, table.ptr, grid, st);
+    }
+    if (class_ms && any) {
+      HF_CUDA(cudaEventRecord(ev[1], st));
+      HF_CUDA(cudaEventSynchronize(ev[1]));
+      float ms = 0.f;
+      HF_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+      class_ms[cls] += ms;
+    }
+  }
+  if (class_ms) {
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+  }
+  HF_CUDA(cudaGetLastError());
+  symmetrize_jk_batch<<<g, 256, 0, st>>>(table.ptr);
+  HF_CUDA(cudaGetLastError());
+  return HF_OK;
+}
+
+int MultiJK::tune(const KernelCommon& kc) {
+  const int cand[3] = {1, 2, 0};
+  double best[HF_NCLASS];
+  int pick[HF_NCLASS];
+  for (int c = 0; c < HF_NCLASS; ++c) {
+    best[c] = 1e300;
+    pick[c] = 0;
+  }
+  for (int k = 0; k < 3; ++k) {
+    for (int c = 0; c < HF_NCLASS; ++c) grid_scale[c] = cand[k];
+    double ms[HF_NCLASS] = {};
+    HF_CHECK(launch(kc, ms));
+    for (int c = 0; c < HF_NCLASS; ++c)
+      if (ms[c] > 0.0 && ms[c] < best[c]) {
+        best[c] = ms[c];
+        pick[c] = cand[k];
+      }
+  }
+  HF_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int c = 0; c < HF_NCLASS; ++c) grid_scale[c] = pick[c];
+  return HF_OK;
+}
+
+int MultiJK::capture(const KernelCommon& kc) {
+  cudaStream_t st = ctx->stream;
+  if (graph_exec) {
+    cudaGraphExecDestroy(graph_exec);
+    graph_exec = nullptr;
+  }
+  if (graph) {
+    cudaGraphDestroy(graph);
+    graph = nullptr;
+  }
+  // make sure the occupancy queries are answered outside the capture
+  for (int c = 0; c < HF_NCLASS; ++c) {
+    ctx->ops[c].occ64();
+    ctx->ops[c].occ32();
+  }
+  HF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const int rc = launch(kc);
+  cudaGraph_t gph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &gph);
+  if (rc != HF_OK) {
+    if (gph) cudaGraphDestroy(gph);
+    return rc;
+  }
+  if (e != cudaSuccess) return hf_fail(HF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  graph = gph;
+  HF_CUDA(cudaGraphInstantiate(&graph_exec, graph, 0));
+  return HF_OK;
+}
+
+int MultiJK::run(const KernelCommon& kc) {
+  if (!graph_exec) return launch(kc);
+  HF_CUDA(cudaGraphLaunch(graph_exec, ctx->stream));
+  return HF_OK;
+}
+
+MultiJK::~MultiJK() {
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  if (graph) cudaGraphDestroy(graph);
+}

@@ -195,6 +195,14 @@ int scf_state_init(hf_basis* b, ScfState& s, int diis_size) {
   HF_CHECK(s.scal.alloc(ctx, 40));
   HF_CHECK(s.islots.alloc(ctx, 16));
   HF_CHECK(s.info.alloc(ctx, 1));
+  if (!s.hscal) {
+    void* hp = nullptr;
+    if (cudaMallocHost(&hp, sizeof(double) * 64 + sizeof(int) * 16) != cudaSuccess)
+      return hf_fail(HF_ERR_OOM, "cudaMallocHost");
+    s.hscal = static_cast<double*>(hp);
+    s.hcoef = s.hscal + 32;
+    s.hslots = reinterpret_cast<int*>(s.hscal + 64);
+  }
   if (s.m > 0) {
     HF_CHECK(s.Fring.alloc(ctx, nn * s.m));
     HF_CHECK(s.Ering.alloc(ctx, nn * s.m));
@@ -245,25 +253,111 @@ int scf_setup(hf_basis* b, ScfState& s) {
   return HF_OK;
 }
 
-// One iteration from the current s.F: diagonalise, new D, J/K, F_k, E_k,
-// DIIS.  Returns E_k via s.energy.
-int scf_iterate(hf_basis* b, ScfState& s, const hf_scf_opts& o, const double* G) {
+// Phase 1 of an iteration (enqueue only): from the current s.F,
+// F' = X F X, eigen-decomposition, C = X C', D = C_occ C_occ^T.
+int scf_density(hf_basis* b, ScfState& s) {
   hf_ctx* ctx = b->ctx;
   cudaStream_t st = ctx->stream;
   const int n = s.n, nocc = b->nelec / 2;
   const size_t nn = (size_t)n * n;
-  // F' = X F X
   HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, s.F.ptr, n, s.X.ptr, n, s.T1.ptr, n));
   HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, s.X.ptr, n, s.T1.ptr, n, s.W.ptr, n));
   HF_CHECK(syevd(ctx, s, s.W.ptr, s.eps.ptr));
-  // C = X C'  (column-major, columns are MOs)
   HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, s.X.ptr, n, s.W.ptr, n, s.C.ptr, n));
-  // D = C_occ C_occ^T
   if (nocc > 0) {
     HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_T, n, n, nocc, s.C.ptr, n, s.C.ptr, n, s.D.ptr, n));
   } else {
     HF_CUDA(cudaMemsetAsync(s.D.ptr, 0, nn * sizeof(double), st));
   }
+  return HF_OK;
+}
+
+// Phase 2 (enqueue only, after J and K of D are in s.J, s.K):
+// F_k = H + 2J - K, E_k, the DIIS error e_k = F D S - S D F, its dot
+// products with the stored errors, and an asynchronous copy of these
+// scalars to pinned host memory (s.hscal).
+int scf_post_jk(hf_basis* b, ScfState& s) {
+  hf_ctx* ctx = b->ctx;
+  cudaStream_t st = ctx->stream;
+  const int n = s.n;
+  const size_t nn = (size_t)n * n;
+  s.fock_builds += 1;
+  k_add_fock<<<blocks(nn), 256, 0, st>>>(s.H.ptr, s.J.ptr, s.K.ptr, s.Fk.ptr, nn);
+  HF_CUDA(cudaMemsetAsync(s.scal.ptr, 0, sizeof(double) * 40, st));
+  k_energy<<<std::min(blocks(nn), 1024u), 256, 0, st>>>(s.D.ptr, s.H.ptr, s.Fk.ptr, nn, s.scal.ptr);
+  HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, s.D.ptr, n, b->S.ptr, n, s.T1.ptr, n));
+  HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, s.Fk.ptr, n, s.T1.ptr, n, s.T2.ptr, n));
+  double* err = s.m > 0 ? s.Ering.ptr + (size_t)s.next * nn : s.T1.ptr;
+  k_antisym<<<blocks(nn), 256, 0, st>>>(s.T2.ptr, err, n, (unsigned long long*)(s.scal.ptr + 1));
+  if (s.m > 0) {
+    HF_CUDA(cudaMemcpyAsync(s.Fring.ptr + (size_t)s.next * nn, s.Fk.ptr, nn * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st));
+    s.slots.push_back(s.next);
+    if ((int)s.slots.size() > s.m) s.slots.erase(s.slots.begin());
+    s.next = (s.next + 1) % s.m;
+    const int k = (int)s.slots.size();
+    for (int i = 0; i < k; ++i) s.hslots[i] = s.slots[i];
+    HF_CUDA(cudaMemcpyAsync(s.islots.ptr, s.hslots, sizeof(int) * k, cudaMemcpyHostToDevice, st));
+    k_multi_dot<<<dim3(std::min(blocks(nn), 64u), k), 256, 0, st>>>(s.Ering.ptr, s.islots.ptr, k, err, nn,
+                                                                    s.scal.ptr + 2);
+  }
+  HF_CUDA(cudaGetLastError());
+  HF_CUDA(cudaMemcpyAsync(s.hscal, s.scal.ptr, sizeof(double) * 18, cudaMemcpyDeviceToHost, st));
+  return HF_OK;
+}
+
+// Phase 3 (after the stream has passed phase 2): energy and DIIS
+// bookkeeping on the host, then enqueue the next F (extrapolated or F_k).
+int scf_diis_step(hf_basis* b, ScfState& s) {
+  hf_ctx* ctx = b->ctx;
+  cudaStream_t st = ctx->stream;
+  const size_t nn = (size_t)s.n * s.n;
+  const double* sc = s.hscal;
+  s.energy = sc[0] + b->e_nuc;
+  s.diis_error = sc[1];  // bit pattern of a non-negative double: ordering preserved by atomicMax
+  if (s.m > 0) {
+    const int k = (int)s.slots.size();
+    for (int i = 0; i < k; ++i)
+      s.Bslot[s.slots[i] * 16 + s.slots[k - 1]] = s.Bslot[s.slots[k - 1] * 16 + s.slots[i]] = sc[2 + i];
+    int first = 0;  // drop the oldest pairs while B is ill-conditioned
+    std::vector<double> c;
+    bool ok = false;
+    while (k - first >= 2) {
+      const int mm = k - first, na = mm + 1;
+      std::vector<double> A(na * na, 0.0), rhs(na, 0.0), w;
+      for (int i = 0; i < mm; ++i)
+        for (int j = 0; j < mm; ++j) A[i * na + j] = s.Bslot[s.slots[first + i] * 16 + s.slots[first + j]];
+      for (int i = 0; i < mm; ++i) A[i * na + mm] = A[mm * na + i] = -1.0;
+      rhs[mm] = -1.0;
+      jacobi_eigs(A, na, w);
+      double amax = 0.0, amin = INFINITY;
+      for (double x : w) {
+        amax = std::max(amax, fabs(x));
+        amin = std::min(amin, fabs(x));
+      }
+      if (amin == 0.0 || amax / amin > 1e14 || !solve_small(A, rhs, na, c)) {
+        ++first;
+        continue;
+      }
+      ok = true;
+      break;
+    }
+    if (ok) {
+      const int mm = k - first;
+      for (int i = 0; i < mm; ++i) s.hcoef[i] = c[i];
+      HF_CUDA(cudaMemcpyAsync(s.scal.ptr + 20, s.hcoef, sizeof(double) * mm, cudaMemcpyHostToDevice, st));
+      k_lincomb<<<blocks(nn), 256, 0, st>>>(s.Fring.ptr, s.islots.ptr + first, s.scal.ptr + 20, mm, nn, s.F.ptr);
+      HF_CUDA(cudaGetLastError());
+      return HF_OK;
+    }
+  }
+  HF_CUDA(cudaMemcpyAsync(s.F.ptr, s.Fk.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return HF_OK;
+}
+
+// One full iteration for a single molecule.
+int scf_iterate(hf_basis* b, ScfState& s, const hf_scf_opts& o, const double* G) {
+  HF_CHECK(scf_density(b, s));
   long long nq = 0;
   if (G) {
     HF_CHECK(hf_jk_stored_device(b, G, s.D.ptr, s.J.ptr, s.K.ptr));
@@ -271,79 +365,9 @@ int scf_iterate(hf_basis* b, ScfState& s, const hf_scf_opts& o, const double* G)
     HF_CHECK(hf_fock_jk_device(b, s.D.ptr, s.J.ptr, s.K.ptr, o.jk, &nq));
   }
   s.quartets += nq;
-  s.fock_builds += 1;
-  k_add_fock<<<blocks(nn), 256, 0, st>>>(s.H.ptr, s.J.ptr, s.K.ptr, s.Fk.ptr, nn);
-  HF_CUDA(cudaMemsetAsync(s.scal.ptr, 0, sizeof(double) * 40, st));
-  k_energy<<<std::min(blocks(nn), 1024u), 256, 0, st>>>(s.D.ptr, s.H.ptr, s.Fk.ptr, nn, s.scal.ptr);
-  // DIIS error e = F D S - S D F (as M - M^T with M = F D S)
-  HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, s.D.ptr, n, b->S.ptr, n, s.T1.ptr, n));
-  HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, s.Fk.ptr, n, s.T1.ptr, n, s.T2.ptr, n));
-  double* err = s.m > 0 ? s.Ering.ptr + (size_t)s.next * nn : s.T1.ptr;
-  k_antisym<<<blocks(nn), 256, 0, st>>>(s.T2.ptr, err, n, (unsigned long long*)(s.scal.ptr + 1));
-  if (s.m > 0) {
-    HF_CUDA(cudaMemcpyAsync(s.Fring.ptr + (size_t)s.next * nn, s.Fk.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice,
-                            st));
-    // slot order: oldest first
-    s.slots.push_back(s.next);
-    if ((int)s.slots.size() > s.m) s.slots.erase(s.slots.begin());
-    s.next = (s.next + 1) % s.m;
-    const int k = (int)s.slots.size();
-    HF_CUDA(cudaMemcpyAsync(s.islots.ptr, s.slots.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
-    k_multi_dot<<<dim3(std::min(blocks(nn), 64u), k), 256, 0, st>>>(s.Ering.ptr, s.islots.ptr, k, err, nn,
-                                                                    s.scal.ptr + 2);
-  }
-  double sc[18];
-  HF_CUDA(cudaMemcpyAsync(sc, s.scal.ptr, sizeof(double) * 18, cudaMemcpyDeviceToHost, st));
-  HF_CUDA(cudaStreamSynchronize(st));
-  s.energy = sc[0] + b->e_nuc;
-  s.diis_error = sc[1];  // bit pattern of a non-negative double: ordering preserved by atomicMax
-  // current F for the next diagonalisation
-  if (s.m > 0) {
-    const int k = (int)s.slots.size();
-    // B rows: dots of the new error (last slot) with all stored, in slot order
-    std::vector<std::vector<double>> Bn(k, std::vector<double>(k));
-    // keep the previous B entries (indexed by slot ids)
-    for (int i = 0; i < k; ++i)
-      for (int j = 0; j < k; ++j) Bn[i][j] = s.Bslot[s.slots[i] * 16 + s.slots[j]];
-    for (int i = 0; i < k; ++i) {
-      Bn[i][k - 1] = Bn[k - 1][i] = sc[2 + i];
-      s.Bslot[s.slots[i] * 16 + s.slots[k - 1]] = s.Bslot[s.slots[k - 1] * 16 + s.slots[i]] = sc[2 + i];
-    }
-    if (k >= 2) {
-      int first = 0;  // drop oldest while ill-conditioned
-      std::vector<double> c;
-      bool ok = false;
-      while (k - first >= 2) {
-        const int mm = k - first, na = mm + 1;
-        std::vector<double> A(na * na, 0.0), rhs(na, 0.0), w;
-        for (int i = 0; i < mm; ++i)
-          for (int j = 0; j < mm; ++j) A[i * na + j] = Bn[first + i][first + j];
-        for (int i = 0; i < mm; ++i) A[i * na + mm] = A[mm * na + i] = -1.0;
-        rhs[mm] = -1.0;
-        jacobi_eigs(A, na, w);
-        double amax = 0.0, amin = INFINITY;
-        for (double x : w) {
-          amax = std::max(amax, fabs(x));
-          amin = std::min(amin, fabs(x));
-        }
-        if (amin == 0.0 || amax / amin > 1e14) { ++first; continue; }
-        if (!solve_small(A, rhs, na, c)) { ++first; continue; }
-        ok = true;
-        break;
-      }
-      if (ok) {
-        const int mm = k - first;
-        HF_CUDA(cudaMemcpyAsync(s.scal.ptr + 20, c.data(), sizeof(double) * mm, cudaMemcpyHostToDevice, st));
-        k_lincomb<<<blocks(nn), 256, 0, st>>>(s.Fring.ptr, s.islots.ptr + first, s.scal.ptr + 20, mm, nn, s.F.ptr);
-        HF_CUDA(cudaGetLastError());
-        // the pinned-free host vector c must outlive the copy
-        HF_CUDA(cudaStreamSynchronize(st));
-        return HF_OK;
-      }
-    }
-  }
-  HF_CUDA(cudaMemcpyAsync(s.F.ptr, s.Fk.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  return HF_OK;
+  HF_CHECK(scf_post_jk(b, s));
+  HF_CUDA(cudaStreamSynchronize(b->ctx->stream));
+  return scf_diis_step(b, s);
 }
 
 int scf_finish(hf_basis* b, ScfState& s, hf_scf_result* r) {

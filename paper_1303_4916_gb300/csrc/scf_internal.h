@@ -18,11 +18,23 @@ struct ScfState {
   double Bslot[16 * 16] = {};
   long long fock_builds = 0, quartets = 0;
   bool have_F1 = false;
+  double* hscal = nullptr;   // pinned: scalars from the device (energy, |e|max, DIIS dots)
+  double* hcoef = nullptr;   // pinned: DIIS coefficients to the device
+  int* hslots = nullptr;     // pinned: DIIS slot order to the device
+  ScfState() = default;
+  ScfState(const ScfState&) = delete;
+  ScfState& operator=(const ScfState&) = delete;
+  ~ScfState() {
+    if (hscal) cudaFreeHost(hscal);
+  }
 };
 
 int scf_state_init(hf_basis* b, ScfState& s, int diis_size);
 int scf_setup(hf_basis* b, ScfState& s);
 int scf_begin(hf_basis* b, ScfState& s, const hf_scf_opts& o, const double* G);
 int scf_iterate(hf_basis* b, ScfState& s, const hf_scf_opts& o, const double* G);
+int scf_density(hf_basis* b, ScfState& s);
+int scf_post_jk(hf_basis* b, ScfState& s);
+int scf_diis_step(hf_basis* b, ScfState& s);
 bool scf_after_iter(hf_basis* b, ScfState& s, const hf_scf_opts& o);
 int scf_finish(hf_basis* b, ScfState& s, hf_scf_result* r);

@@ -1,0 +1,123 @@
+"""Batched SCF and the continuous-batching server against single-molecule
+solves and the oracle: every molecule's result is the same alone and in the
+mix (|dE| <= 1e-8 Eh), failures stay with their own request."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import lattice_molecule
+from synth.molecules import _pack
+
+pytestmark = pytest.mark.gpu
+E_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def hf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1303_4916_gb300 as hf
+    return hf
+
+
+@pytest.fixture(scope="module")
+def ctx(hf):
+    return hf.Context(0)
+
+
+def _mols():
+    return [lattice_molecule(n, s, r) for n, s, r in
+            [(3, 51, "sp"), (5, 52, "sp"), (4, 53, "spd"), (6, 54, "sp"), (2, 55, "spd"), (7, 56, "sp")]]
+
+
+def _lindep():
+    return _pack([1, 1], [[0, 0, 0], [1.4, 0, 0]], [(0, 0, [1.0], [1.0]), (0, 0, [1.0], [1.0]), (1, 0, [1.0], [1.0])],
+                 "dup", 0, n_electrons=2)
+
+
+def test_batch_matches_single_and_oracle(ctx, hf):
+    mols = _mols()
+    alone = [hf.Basis(ctx, m).scf(max_iter=128, e_tol=1e-10, diis_size=8) for m in mols]
+    bases = [hf.Basis(ctx, m) for m in mols]
+    res, st = hf.scf_solve_batch(bases, max_iter=128, e_tol=1e-10, diis_size=8)
+    for a, r, s in zip(alone, res, st):
+        assert s == 0 and r.converged
+        assert abs(r.energy - a.energy) <= E_TOL
+        assert abs(r.iterations - a.iterations) <= 1
+    for k in (0, 2):
+        ro = oracle.rhf(mols[k], max_iter=128, e_tol=1e-10, diis_size=8, tau=1e-12, nthreads=oracle.oracle_threads())
+        assert abs(res[k].energy - ro.energy) <= E_TOL
+
+
+def test_batch_failure_stays_local(ctx, hf):
+    mols = [lattice_molecule(3, 61, "sp"), _lindep(), lattice_molecule(4, 62, "sp")]
+    bases = [hf.Basis(ctx, m) for m in mols]
+    with pytest.raises(hf.HFError):
+        hf.scf_solve_batch(bases)
+    import ctypes
+    from paper_1303_4916_gb300 import _abi
+    lib = hf.load()
+    arr = (ctypes.c_void_p * 3)(*[b.handle.value for b in bases])
+    res = (_abi.hf_scf_result * 3)()
+    st = (ctypes.c_int * 3)()
+    rc = lib.hf_scf_solve_batch(arr, 3, None, res, st)
+    assert rc == _abi.HF_ERR_LINDEP
+    assert list(st) == [0, _abi.HF_ERR_LINDEP, 0]
+    for k in (0, 2):
+        a = hf.Basis(ctx, mols[k]).scf()
+        assert abs(res[k].energy - a.energy) <= E_TOL
+
+
+def test_serve_mix_equals_alone(ctx, hf):
+    mols = _mols()
+    alone = [hf.Basis(ctx, m).scf(max_iter=128, e_tol=1e-10, diis_size=8).energy for m in mols]
+    srv = hf.Server(ctx, max_active=4, max_iter=128, e_tol=1e-10, diis_size=8)
+    tickets = [srv.submit(m) for m in mols[:3]]
+    time.sleep(0.05)                     # the first ones are running when the rest arrive
+    tickets += [srv.submit(m) for m in mols[3:]]
+    bad = srv.submit(_lindep())
+    srv.drain(600)
+    results = [srv.poll(t) for t in tickets]
+    for r, e in zip(results, alone):
+        assert r is not None and r.status == 0 and r.converged
+        assert abs(r.energy - e) <= E_TOL
+        assert r.t_submit <= r.t_admit <= r.t_done
+    rb = srv.poll(bad)
+    assert rb.status == -4
+    # continuous batching: a later arrival was admitted before an earlier one finished
+    assert min(r.t_admit for r in results[3:]) < max(r.t_done for r in results[:3])
+    from paper_1303_4916_gb300 import _abi
+    assert hf.load().hf_serve_poll(srv._h, tickets[0], None) == _abi.HF_ERR_NOT_FOUND
+    srv.close()
+
+
+def test_serve_queue_limits(ctx, hf):
+    from paper_1303_4916_gb300 import _abi
+    srv = hf.Server(ctx, max_active=1, queue_capacity=2)
+    m = lattice_molecule(6, 71, "sp")
+    codes = []
+    tickets = []
+    for _ in range(5):
+        try:
+            tickets.append(srv.submit(m))
+            codes.append(0)
+        except hf.HFError as e:
+            codes.append(e.code)
+    assert _abi.HF_ERR_QUEUE_FULL in codes
+    # cancel whatever is still queued (not yet admitted)
+    cancelled = [t for t in tickets if srv.cancel(t) == 0]
+    for t in cancelled:
+        assert hf.load().hf_serve_poll(srv._h, t, None) == _abi.HF_ERR_NOT_FOUND
+    with pytest.raises(hf.HFError) as e:
+        srv.submit(m, n_electrons=3)
+    assert e.value.code == _abi.HF_ERR_ODD_ELECTRONS
+    srv.drain(600)
+    srv.close()
+    tiny = hf.Server(ctx, hbm_budget=1 << 20)
+    with pytest.raises(hf.HFError) as e:
+        tiny.submit(lattice_molecule(40, 1, "sp"))
+    assert e.value.code == _abi.HF_ERR_TOO_LARGE
+    tiny.close()
