@@ -83,12 +83,12 @@ void hf_dev_free(hf_ctx* ctx, void* p, size_t bytes) {
 }
 
 // ------------------------------------------------------------- Boys table
-// Row i: F_m(T_i), m = 0..BOYS_NM-1, and exp(-T_i), T_i = i*BOYS_H, in long
-// double: F_{NM-1}(T) from its power series
+// F_m(T), m = 0..BOYS_NM-1, and exp(-T) in long double: F_{NM-1}(T) from its
+// power series
 //   F_m(T) = exp(-T) sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)),
 // the lower orders by the downward recursion F_m = (2T F_{m+1} + e^{-T})/(2m+1),
 // which is stable in that direction.
-static void boys_row(long double T, long double* out) {
+static void boys_row(long double T, long double* F, long double* et) {
   const int M = BOYS_NM - 1;
   long double term = 1.0L / (2 * M + 1), sum = term;
   for (int k = 1; k < 5000; ++k) {
@@ -96,30 +96,42 @@ static void boys_row(long double T, long double* out) {
     sum += term;
     if (term <= sum * 1e-21L) break;
   }
-  const long double et = expl(-T);
-  out[M] = et * sum;
-  for (int m = M - 1; m >= 0; --m) out[m] = (2.0L * T * out[m + 1] + et) / (long double)(2 * m + 1);
-  out[BOYS_NM] = et;
+  *et = expl(-T);
+  F[M] = *et * sum;
+  for (int m = M - 1; m >= 0; --m) F[m] = (2.0L * T * F[m + 1] + *et) / (long double)(2 * m + 1);
 }
 
 int hf_boys_tables(hf_ctx* ctx) {
-  std::vector<double> t64((size_t)BOYS_NGRID * BOYS_STRIDE);
-  std::vector<float> t32((size_t)BOYS_NGRID * BOYS_STRIDE);
-  long double row[BOYS_STRIDE];
+  const size_t n64 = (size_t)(BOYS_LMAX + 1) * BOYS_NGRID * BOYS64_ROW;
+  const size_t n32 = (size_t)(BOYS_LMAX + 1) * BOYS_NGRID * BOYS32_ROW;
+  std::vector<double> t64(n64);
+  std::vector<float> t32(n32);
+  long double F[BOYS_NM], et;
+  long double fact[BOYS64_TERMS];
+  fact[0] = 1.0L;
+  for (int k = 1; k < BOYS64_TERMS; ++k) fact[k] = fact[k - 1] * k;
   for (int i = 0; i < BOYS_NGRID; ++i) {
-    boys_row((long double)i * (long double)BOYS_H, row);
-    for (int k = 0; k < BOYS_STRIDE; ++k) {
-      t64[(size_t)i * BOYS_STRIDE + k] = (double)row[k];
-      t32[(size_t)i * BOYS_STRIDE + k] = (float)row[k];
+    boys_row((long double)((double)i * BOYS_H), F, &et);
+    for (int L = 0; L <= BOYS_LMAX; ++L) {
+      double* r = &t64[((size_t)L * BOYS_NGRID + i) * BOYS64_ROW];
+      for (int k = 0; k < BOYS64_TERMS; ++k) {
+        r[k] = (double)(F[L + k] / fact[k]);
+        r[BOYS64_TERMS + k] = (double)(et / fact[k]);
+      }
+      float* f = &t32[((size_t)L * BOYS_NGRID + i) * BOYS32_ROW];
+      for (int k = 0; k < BOYS32_TERMS; ++k) {
+        f[k] = (float)(F[L + k] / fact[k]);
+        f[BOYS32_TERMS + k] = (float)(et / fact[k]);
+      }
     }
   }
   void* p = nullptr;
-  HF_CHECK(hf_dev_alloc(ctx, &p, t64.size() * sizeof(double)));
+  HF_CHECK(hf_dev_alloc(ctx, &p, n64 * sizeof(double)));
   ctx->boys64 = (double*)p;
-  HF_CHECK(hf_dev_alloc(ctx, &p, t32.size() * sizeof(float)));
+  HF_CHECK(hf_dev_alloc(ctx, &p, n32 * sizeof(float)));
   ctx->boys32 = (float*)p;
-  HF_CUDA(cudaMemcpyAsync(ctx->boys64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  HF_CUDA(cudaMemcpyAsync(ctx->boys32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  HF_CUDA(cudaMemcpyAsync(ctx->boys64, t64.data(), n64 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  HF_CUDA(cudaMemcpyAsync(ctx->boys32, t32.data(), n32 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   HF_CUDA(cudaStreamSynchronize(ctx->stream));
   return HF_OK;
 }

@@ -514,10 +514,11 @@ int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const 
 }
 
 // Operations per primitive quartet outside the VRR: p+q, 1/sqrt, 1/(p+q),
-// rho/p, rho/q, PQ, WP, WQ, T, prefactor (22), the Boys evaluation (Taylor
-// 14 per order for L <= 1; else 14 + exp 18 + 3L), scaling of B (L+1).
+// rho/p, rho/q, PQ, WP, WQ, T, prefactor (22), the Boys evaluation (index
+// 3, Horner 14 per order for L <= 1; else 3 + 14 + exp 14 + 3L), scaling
+// of B (L+1).
 static int prim_overhead_flops(int L) {
-  const int boys = L <= 1 ? 14 * (L + 1) : 14 + 18 + 3 * L;
+  const int boys = L <= 1 ? 3 + 14 * (L + 1) : 3 + 14 + 14 + 3 * L;
   return 22 + boys + (L + 1);
 }
 

@@ -28,43 +28,44 @@
 namespace hfk {
 
 // ------------------------------------------------------------- Boys function
-// Table: row i holds F_m(T_i), m = 0..BOYS_NM-1, then exp(-T_i), with
-// T_i = i * BOYS_H.  For T < BOYS_TMAX: Taylor expansion about the nearest
-// grid point, F_m(T_i - x) = sum_k F_{m+k}(T_i) x^k / k! (since
-// dF_m/dT = -F_{m+1}), 8 terms; exp(-T) = exp(-T_i) exp(x) likewise; then
+// For T < BOYS_TMAX, with T_i the nearest grid point and x = T_i - T
+// (|x| <= BOYS_H/2): F_m(T) = sum_k F_{m+k}(T_i) x^k / k!  (dF_m/dT =
+// -F_{m+1}) by Horner on the pre-divided coefficients of slice m, 8 terms
+// (truncation below 1e-15 relative).  For L <= 1 every order is taken this
+// way; for L >= 2 only F_L, then exp(-T) = exp(-T_i) e^x the same way and
 // the downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1).  For
-// T >= BOYS_TMAX: F_0 = sqrt(pi/T)/2 and F_{m+1} = (2m+1) F_m / (2T), the
-// neglected exp(-T) terms being below 1e-26.
+// T >= BOYS_TMAX: F_0 = sqrt(pi/T)/2 and F_{m+1} = (2m+1) F_m / (2T); the
+// neglected exp(-T) terms are below 1e-26.
+// The row index is rounded with the 1.5 * 2^52 shifter (no conversions):
+// the low word of T/h + 1.5 * 2^52 is round(T/h).
+#define HF_ROUND_SHIFTER 6755399441055744.0
+
+__device__ __forceinline__ double boys_horner64(const double* __restrict__ c, double x) {
+  const double2* c2 = reinterpret_cast<const double2*>(c);
+  const double2 a = __ldg(c2), b = __ldg(c2 + 1), d = __ldg(c2 + 2), e = __ldg(c2 + 3);
+  double f = e.y;
+  f = fma(f, x, e.x);
+  f = fma(f, x, d.y);
+  f = fma(f, x, d.x);
+  f = fma(f, x, b.y);
+  f = fma(f, x, b.x);
+  f = fma(f, x, a.y);
+  return fma(f, x, a.x);
+}
+
 template <int L>
 __device__ __forceinline__ void boys64(double T, const double* __restrict__ tab, double* F) {
   if (T < BOYS_TMAX) {
-    const int i = __double2int_rn(T * (1.0 / BOYS_H));
-    const double x = (double)i * BOYS_H - T;  // T = T_i - x
-    const double* __restrict__ r = tab + i * BOYS_STRIDE;
+    const double y = fma(T, 1.0 / BOYS_H, HF_ROUND_SHIFTER);
+    const int i = __double2loint(y);
+    const double x = fma(y - HF_ROUND_SHIFTER, BOYS_H, -T);
     if (L <= 1) {
 #pragma unroll
-      for (int m = 0; m <= L; ++m) {
-        double f = __ldg(r + m + 7);
-#pragma unroll
-        for (int k = 7; k >= 1; --k) f = fma(f, x * (1.0 / k), __ldg(r + m + k - 1));
-        F[m] = f;
-      }
+      for (int m = 0; m <= L; ++m) F[m] = boys_horner64(tab + ((size_t)m * BOYS_NGRID + i) * BOYS64_ROW, x);
     } else {
-      double f = __ldg(r + L + 7);
-#pragma unroll
-      for (int k = 7; k >= 1; --k) f = fma(f, x * (1.0 / k), __ldg(r + L + k - 1));
-      F[L] = f;
-      // exp(x), |x| <= BOYS_H/2, 9 terms
-      double e = 1.0 / 40320.0;
-      e = fma(e, x, 1.0 / 5040.0);
-      e = fma(e, x, 1.0 / 720.0);
-      e = fma(e, x, 1.0 / 120.0);
-      e = fma(e, x, 1.0 / 24.0);
-      e = fma(e, x, 1.0 / 6.0);
-      e = fma(e, x, 0.5);
-      e = fma(e, x, 1.0);
-      e = fma(e, x, 1.0);
-      e *= __ldg(r + BOYS_NM);
+      const double* __restrict__ r = tab + ((size_t)L * BOYS_NGRID + i) * BOYS64_ROW;
+      F[L] = boys_horner64(r, x);
+      const double e = boys_horner64(r + BOYS64_TERMS, x);
       const double t2 = 2.0 * T;
 #pragma unroll
       for (int m = L - 1; m >= 0; --m) F[m] = fma(t2, F[m + 1], e) * (1.0 / (2 * m + 1));
@@ -80,32 +81,26 @@ __device__ __forceinline__ void boys64(double T, const double* __restrict__ tab,
 
 // FP32 evaluation of the same expansion, 5 terms (truncation below 3e-9
 // relative), for the reduced-precision quartets when requested.
+__device__ __forceinline__ float boys_horner32(const float* __restrict__ c, float x) {
+  float f = __ldg(c + 4);
+  f = fmaf(f, x, __ldg(c + 3));
+  f = fmaf(f, x, __ldg(c + 2));
+  f = fmaf(f, x, __ldg(c + 1));
+  return fmaf(f, x, __ldg(c));
+}
+
 template <int L>
 __device__ __forceinline__ void boys32(float T, const float* __restrict__ tab, float* F) {
   if (T < (float)BOYS_TMAX) {
     const int i = __float2int_rn(T * (float)(1.0 / BOYS_H));
     const float x = (float)i * (float)BOYS_H - T;
-    const float* __restrict__ r = tab + i * BOYS_STRIDE;
     if (L <= 1) {
 #pragma unroll
-      for (int m = 0; m <= L; ++m) {
-        float f = __ldg(r + m + 4);
-#pragma unroll
-        for (int k = 4; k >= 1; --k) f = fmaf(f, x * (1.0f / k), __ldg(r + m + k - 1));
-        F[m] = f;
-      }
+      for (int m = 0; m <= L; ++m) F[m] = boys_horner32(tab + ((size_t)m * BOYS_NGRID + i) * BOYS32_ROW, x);
     } else {
-      float f = __ldg(r + L + 4);
-#pragma unroll
-      for (int k = 4; k >= 1; --k) f = fmaf(f, x * (1.0f / k), __ldg(r + L + k - 1));
-      F[L] = f;
-      float e = 1.0f / 120.0f;
-      e = fmaf(e, x, 1.0f / 24.0f);
-      e = fmaf(e, x, 1.0f / 6.0f);
-      e = fmaf(e, x, 0.5f);
-      e = fmaf(e, x, 1.0f);
-      e = fmaf(e, x, 1.0f);
-      e *= __ldg(r + BOYS_NM);
+      const float* __restrict__ r = tab + ((size_t)L * BOYS_NGRID + i) * BOYS32_ROW;
+      F[L] = boys_horner32(r, x);
+      const float e = boys_horner32(r + BOYS32_TERMS, x);
       const float t2 = 2.0f * T;
 #pragma unroll
       for (int m = L - 1; m >= 0; --m) F[m] = fmaf(t2, F[m + 1], e) * (1.0f / (2 * m + 1));

@@ -3,14 +3,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-// Boys table: rows T_i = i * BOYS_H for i = 0 .. BOYS_NGRID-1; each row
-// holds F_0..F_{BOYS_NM-1}(T_i) and exp(-T_i).  Lookups use the nearest
-// row, so T < BOYS_TMAX keeps the row index inside the table.
+// Boys tables.  Grid T_i = i * BOYS_H (the double product), i = 0 ..
+// BOYS_NGRID-1; lookups use the nearest row, so T < BOYS_TMAX stays inside.
+// One slice per order L = 0..BOYS_LMAX; row i of slice L holds the Taylor
+// coefficients about T_i of F_L, F_{L+k}(T_i)/k! for k < TERMS (from
+// dF_m/dT = -F_{m+1}), followed by those of exp(-T), exp(-T_i)/k!.
+// FP64: 8 + 8 coefficients per 128-byte row; FP32: 5 + 5.
 #define BOYS_H 0.1
 #define BOYS_NGRID 602
 #define BOYS_TMAX 60.0
+#define BOYS_LMAX 8
 #define BOYS_NM 16
-#define BOYS_STRIDE (BOYS_NM + 1)
+#define BOYS64_TERMS 8
+#define BOYS64_ROW 16
+#define BOYS32_TERMS 5
+#define BOYS32_ROW 10
 
 // Primitive-pair record, FP64: p, 1/(2p), P[3], PA[3], K, pad (80 bytes);
 // FP32: the same nine values then three pads (48 bytes).
