@@ -341,6 +341,222 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------- other workloads
+# Secondary measurements (not the driver's default line): each prints one
+# JSON line of its own.
+
+def _ctx_basis(mol, hf):
+    ctx = hf.Context(0)
+    return ctx, hf.Basis(ctx, mol)
+
+
+def run_c1(args):
+    """8-atom H chain (seed 0): RHF, DIIS off, direct and stored-tensor J/K."""
+    import torch
+    import paper_1303_4916_gb300 as hf
+    from synth import h_line
+    mol = h_line()
+    ctx, basis = _ctx_basis(mol, hf)
+    out = {"workload": "8-atom H chain (seed 0), nbf 8, RHF DIIS off, max 30 iterations"}
+    for stored in (False, True):
+        basis.scf(max_iter=30, e_tol=1e-8, diis_size=0, schwarz_tau=0.0, stored_eri=stored)
+        t0 = time.perf_counter()
+        r = basis.scf(max_iter=30, e_tol=1e-8, diis_size=0, schwarz_tau=0.0, stored_eri=stored)
+        out["stored" if stored else "direct"] = {"scf_latency_s": time.perf_counter() - t0,
+                                                 "iterations": r.iterations, "energy": r.energy}
+    D = r.tensors["D"]
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    opts = hf.jk_opts(schwarz_tau=0.0)
+    for _ in range(5):
+        basis.fock_jk(D, J, K, opts)
+    torch.cuda.synchronize()
+    n = 200
+    t0 = time.perf_counter()
+    for _ in range(n):
+        basis.fock_jk(D, J, K, opts)
+    torch.cuda.synchronize()
+    out["direct_builds_per_s"] = n / (time.perf_counter() - t0)
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "value": out["direct_builds_per_s"], "dtype": "f64",
+                      "data": "synthetic", "config": out}), flush=True)
+
+
+def run_c3(args):
+    """150-atom s+p+d lattice (seed 2): FP64 J/K build versus the precision
+    split (Schwarz bound < 1e-5 in FP32), at the density of iteration 1."""
+    import torch
+    import paper_1303_4916_gb300 as hf
+    from synth import lattice_molecule
+    mol = lattice_molecule(150, 2, "spd")
+    t0 = time.perf_counter()
+    ctx, basis = _ctx_basis(mol, hf)
+    setup_s = time.perf_counter() - t0
+    mixed = hf.jk_opts(schwarz_tau=1e-12, fp32_bound=1e-5)
+    plain = hf.jk_opts(schwarz_tau=1e-12)
+    nq, nf = basis.count_quartets(mixed)
+
+    def est_seconds(o, tflops64=0.6, tflops32=20.0):
+        t = 0.0
+        for st in basis.class_stats(o):
+            t += (st.prim_quartets_fp64 * st.prim_flops + st.quartets_fp64 * (st.hrr_flops + st.digest_flops)) / (tflops64 * 1e12)
+            t += (st.prim_quartets_fp32 * st.prim_flops + st.quartets_fp32 * (st.hrr_flops + st.digest_flops)) / (tflops32 * 1e12)
+        return t
+    est = {"fp64": est_seconds(plain), "mixed": est_seconds(mixed)}
+    print(json.dumps({"c3_estimate_s_per_build": est, "quartets": nq, "quartets_fp32": nf, "nbf": basis.nbf}),
+          flush=True)
+    if max(est.values()) > args.c3_max_seconds:
+        print(json.dumps({"skipped": f"estimated build time above --c3-max-seconds {args.c3_max_seconds}"}))
+        return 0
+    r = basis.scf(max_iter=1, e_tol=1e-8, diis_size=0, fp32_bound=1e-5)   # D_1 from diagonalising H
+    D = r.tensors["D"]
+    res = {}
+    for name, o in (("mixed", mixed), ("fp64", plain)):
+        J = torch.empty_like(D)
+        K = torch.empty_like(D)
+        basis.fock_jk(D, J, K, o)
+        torch.cuda.synchronize()
+        steps = max(1, args.steps if name == "mixed" else 1)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            basis.fock_jk(D, J, K, o)
+        torch.cuda.synchronize()
+        res[name] = {"builds_per_s": steps / (time.perf_counter() - t0), "F": 2 * J - K}
+    dF = float((res["mixed"]["F"] - res["fp64"]["F"]).abs().max())
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "value": res["mixed"]["builds_per_s"], "dtype": "f64+f32",
+                      "data": "synthetic",
+                      "config": {"workload": f"150-atom s+p+d lattice (seed 2), nbf {basis.nbf}, density of RHF "
+                                             f"iteration 1, Schwarz 1e-12, FP32 below bound 1e-5",
+                                 "quartets": nq, "quartets_fp32": nf, "setup_s": setup_s},
+                      "fp64_builds_per_s": res["fp64"]["builds_per_s"],
+                      "speedup_mixed_vs_fp64": res["mixed"]["builds_per_s"] / res["fp64"]["builds_per_s"],
+                      "max_abs_dF_mixed_vs_fp64": dF}), flush=True)
+
+
+def run_batch(args):
+    """Batched SCF of the first --nmol molecules of the 512-molecule stream
+    (atoms U[4,60], s+p rules, seeds 1000+i) versus a loop of single-molecule
+    FP64 solves."""
+    import paper_1303_4916_gb300 as hf
+    from synth import batch_molecules
+    mols = batch_molecules(512)[: args.nmol]
+    ctx = hf.Context(0)
+    bases = [hf.Basis(ctx, m) for m in mols]
+    t0 = time.perf_counter()
+    plain = [b.scf(max_iter=128, e_tol=1e-8, diis_size=8, outputs=False) for b in bases]
+    t_plain = time.perf_counter() - t0
+    out = {}
+    for name, fb in (("batch_fp64", 0.0), ("batch_mixed", 1e-5)):
+        t0 = time.perf_counter()
+        res, st = hf.scf_solve_batch(bases, max_iter=128, e_tol=1e-8, diis_size=8, fp32_bound=fb)
+        dt = time.perf_counter() - t0
+        builds = sum(r.fock_builds for r in res)
+        both = [(r, p) for r, p in zip(res, plain) if r.converged and p.converged]
+        out[name] = {"seconds": dt, "mol_fock_builds_per_s": builds / dt, "scf_per_s": len(res) / dt,
+                     "converged": int(sum(r.converged for r in res)),
+                     "max_abs_dE_vs_plain_both_converged": max(abs(r.energy - p.energy) for r, p in both),
+                     "n_both_converged": len(both),
+                     "n_dE_above_1e-8": int(sum(abs(r.energy - p.energy) > 1e-8 for r, p in both))}
+    pb = sum(p.fock_builds for p in plain)
+    line = {"metric": "molecule Fock builds/s", "unit": "builds/s", "value": out["batch_mixed"]["mol_fock_builds_per_s"],
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"first {len(mols)} of 512 molecules, atoms U[4,60], s+p, seeds 1000+i",
+                       "nbf_total": int(sum(b.nbf for b in bases))},
+            "plain_loop": {"seconds": t_plain, "mol_fock_builds_per_s": pb / t_plain, "scf_per_s": len(mols) / t_plain,
+                           "converged": int(sum(p.converged for p in plain))},
+            **out}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Open-loop replay of the first --nreq requests of the Poisson stream
+    (mean 200/s, seed 7; atoms log-uniform [4, --atoms-max], s+p+d rules,
+    molecule seeds 10000+i) through the server with the precision split,
+    and through a FIFO loop of single-molecule FP64 solves on the same
+    arrival times."""
+    import threading as th
+    import paper_1303_4916_gb300 as hf
+    from synth import lattice_molecule, serve_stream
+    t_arr, sizes, seeds = serve_stream(args.nreq, atoms=(4, args.atoms_max))
+    mols = [lattice_molecule(int(n), int(s), "spd") for n, s in zip(sizes, seeds)]
+    ctx = hf.Context(0)
+    srv = hf.Server(ctx, max_active=args.max_active, fp32_bound=1e-5)
+    tickets = [None] * len(mols)
+    t_start = time.perf_counter()
+
+    def feeder():
+        for i, m in enumerate(mols):
+            d = t_arr[i] - (time.perf_counter() - t_start)
+            if d > 0:
+                time.sleep(d)
+            tickets[i] = srv.submit(m)
+    f = th.Thread(target=feeder)
+    f.start()
+    f.join()
+    srv.drain(args.serve_timeout)
+    wall = time.perf_counter() - t_start
+    lat, builds, energies = [], 0, []
+    for t in tickets:
+        r = srv.poll(t)
+        lat.append(r.t_done - r.t_submit)
+        builds += r.fock_builds
+        energies.append(r.energy)
+    srv.close()
+    # the same stream through the plain FP64 single-molecule path, FIFO
+    end = 0.0
+    lat_plain, e_plain = [], []
+    for i, m in enumerate(mols):
+        b = hf.Basis(ctx, m)
+        t0 = time.perf_counter()
+        r = b.scf(max_iter=128, e_tol=1e-8, diis_size=8, outputs=False)
+        dt = time.perf_counter() - t0
+        start = max(t_arr[i], end)
+        end = start + dt
+        lat_plain.append(end - t_arr[i])
+        e_plain.append(r.energy)
+    q = lambda v, p: float(np.percentile(np.array(v), p))
+    print(json.dumps({"metric": "p99 SCF latency", "unit": "s", "value": q(lat, 99), "higher_is_better": False,
+                      "dtype": "f64+f32", "data": "synthetic",
+                      "config": {"workload": f"first {len(mols)} requests of the Poisson stream (200/s), atoms "
+                                             f"logU[4,{args.atoms_max}], s+p+d", "max_active": args.max_active},
+                      "served": {"p50_s": q(lat, 50), "p99_s": q(lat, 99), "solves_per_s": len(mols) / wall,
+                                 "fock_builds_per_s": builds / wall,
+                                 "offered_per_s": len(mols) / max(t_arr[-1], 1e-9)},
+                      "plain_fifo": {"p50_s": q(lat_plain, 50), "p99_s": q(lat_plain, 99),
+                                     "solves_per_s": len(mols) / end},
+                      "max_abs_dE_served_vs_plain": float(np.max(np.abs(np.array(energies) - np.array(e_plain))))}),
+          flush=True)
+
+
+def run_classes(args):
+    """Per-class kernel time and achieved FP64 rate on an s+p+d lattice
+    molecule (--natom atoms, seed 3), one J/K build at a seeded density."""
+    import torch
+    import paper_1303_4916_gb300 as hf
+    from synth import lattice_molecule
+    mol = lattice_molecule(args.natom, 3, "spd")
+    ctx, basis = _ctx_basis(mol, hf)
+    n = basis.nbf
+    rng = np.random.default_rng(0)
+    C = rng.normal(size=(n, max(1, mol.n_electrons // 2))) / np.sqrt(n)
+    D = torch.tensor(C @ C.T, device="cuda:0")
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    o = hf.jk_opts(schwarz_tau=1e-12, fp32_bound=args.fp32_bound)
+    basis.fock_jk_profiled(D, J, K, o)
+    ms = np.mean([basis.fock_jk_profiled(D, J, K, o) for _ in range(3)], axis=0)
+    rows = []
+    for c, st in enumerate(basis.class_stats(o)):
+        name = f"({'spd'[st.la]}{'spd'[st.lb]}|{'spd'[st.lc]}{'spd'[st.ld]})"
+        for r, (q, pq) in enumerate(((st.quartets_fp64, st.prim_quartets_fp64), (st.quartets_fp32, st.prim_quartets_fp32))):
+            if q == 0:
+                continue
+            fl = pq * st.prim_flops + q * (st.hrr_flops + st.digest_flops)
+            rows.append({"class": name, "precision": "fp32" if r else "fp64", "quartets": q, "prim_quartets": pq,
+                         "ms": float(ms[c, r]), "tflops": fl / (ms[c, r] * 1e-3) / 1e12 if ms[c, r] > 0 else None})
+    print(json.dumps({"workload": f"{args.natom}-atom s+p+d lattice (seed 3), nbf {n}", "fp32_bound": args.fp32_bound,
+                      "total_ms": float(ms.sum()), "classes": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,11 +565,24 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "batch", "serve", "classes"],
+                    help="c2 (default) is the benchmark line; the others print secondary measurements")
+    ap.add_argument("--nmol", type=int, default=64)
+    ap.add_argument("--nreq", type=int, default=100)
+    ap.add_argument("--atoms-max", type=int, default=150)
+    ap.add_argument("--max-active", type=int, default=32)
+    ap.add_argument("--serve-timeout", type=float, default=1800.0)
+    ap.add_argument("--c3-max-seconds", type=float, default=120.0)
+    ap.add_argument("--natom", type=int, default=12)
+    ap.add_argument("--fp32-bound", type=float, default=0.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "c2":
+        return {"c1": run_c1, "c3": run_c3, "batch": run_batch, "serve": run_serve,
+                "classes": run_classes}[args.workload](args)
     return run_ours(args)
 
 

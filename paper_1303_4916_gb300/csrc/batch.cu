@@ -6,8 +6,8 @@
 // replayed from a CUDA graph), then the per-molecule Fock/energy/DIIS
 // updates are enqueued, with a single host synchronisation per iteration
 // for all molecules.  Converged molecules drop out of the launches (their
-// work items are skipped) and retire.  Before the first iteration the
-// autotuner picks the blocks-per-SM of each class from three timed builds.
+// work items are skipped) and retire.  The first three iterations double
+// as the autotuner's trials of the launch shape (blocks per SM) of each class.
 #include <chrono>
 #include <memory>
 #include <vector>
@@ -62,12 +62,15 @@ extern "C" int hf_scf_solve_batch(hf_basis* const* bases, int count, const hf_sc
   while (nactive > 0) {
     for (int i = 0; i < count; ++i)
       if (active[i]) HF_CHECK(scf_density(mols[i], *S[i]));
-    if (!tuned) {
-      HF_CHECK(mj.tune(kc));    // times three builds of the first iteration's densities
-      HF_CHECK(mj.capture(kc));
-      tuned = true;
+    if (!mj.tuned) {
+      HF_CHECK(mj.tune_step(kc));   // iterations 1-3 time the candidate launch shapes
+    } else {
+      if (!tuned) {
+        HF_CHECK(mj.capture(kc));   // then the J/K phase is replayed from a graph
+        tuned = true;
+      }
+      HF_CHECK(mj.run(kc));
     }
-    HF_CHECK(mj.run(kc));
     for (int i = 0; i < count; ++i)
       if (active[i]) {
         S[i]->quartets += mj.mol_quartets[i];

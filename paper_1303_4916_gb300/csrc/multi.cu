@@ -162,26 +162,19 @@ int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
   return HF_OK;
 }
 
-int MultiJK::tune(const KernelCommon& kc) {
-  const int cand[3] = {1, 2, 0};
-  double best[HF_NCLASS];
-  int pick[HF_NCLASS];
-  for (int c = 0; c < HF_NCLASS; ++c) {
-    best[c] = 1e300;
-    pick[c] = 0;
+int MultiJK::tune_step(const KernelCommon& kc) {
+  static const int cand[3] = {0, 2, 1};
+  for (int c = 0; c < HF_NCLASS; ++c) grid_scale[c] = cand[tune_iter];
+  HF_CHECK(launch(kc, tune_ms[tune_iter]));
+  if (++tune_iter == 3) {
+    for (int c = 0; c < HF_NCLASS; ++c) {
+      int best = 0;
+      for (int k = 1; k < 3; ++k)
+        if (tune_ms[k][c] > 0.0 && tune_ms[k][c] < tune_ms[best][c]) best = k;
+      grid_scale[c] = cand[best];
+    }
+    tuned = true;
   }
-  for (int k = 0; k < 3; ++k) {
-    for (int c = 0; c < HF_NCLASS; ++c) grid_scale[c] = cand[k];
-    double ms[HF_NCLASS] = {};
-    HF_CHECK(launch(kc, ms));
-    for (int c = 0; c < HF_NCLASS; ++c)
-      if (ms[c] > 0.0 && ms[c] < best[c]) {
-        best[c] = ms[c];
-        pick[c] = cand[k];
-      }
-  }
-  HF_CUDA(cudaStreamSynchronize(ctx->stream));
-  for (int c = 0; c < HF_NCLASS; ++c) grid_scale[c] = pick[c];
   return HF_OK;
 }
 

@@ -31,9 +31,15 @@ struct MultiJK {
   // class_ms, each class launch is bracketed by events and its duration in
   // ms is added to class_ms[cls] (the caller synchronises).
   int launch(const KernelCommon& kc, double* class_ms = nullptr);
-  // Autotuner: time every class at 1, 2 and full-occupancy blocks per SM and
-  // keep the fastest per class.  Runs three J/K builds of the current set.
-  int tune(const KernelCommon& kc);
+  // Autotuner, online: each call runs one J/K build of the current set with
+  // the next candidate blocks-per-SM setting (full occupancy, 2, 1), timing
+  // every class with events; after the last candidate each class keeps its
+  // fastest setting.  The builds are the SCF's own iterations (same quartet
+  // work each time), so tuning costs no extra builds.
+  int tune_step(const KernelCommon& kc);
+  bool tuned = false;
+  int tune_iter = 0;
+  double tune_ms[3][HF_NCLASS] = {};
   // Capture launch() into a CUDA graph (replayed by run()); the graph stays
   // valid across set_active() since only the table's contents change.
   int capture(const KernelCommon& kc);

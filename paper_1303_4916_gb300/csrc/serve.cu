@@ -167,11 +167,14 @@ void hf_server::run() {
     for (Request* r : active)
       if (rc == HF_OK) rc = scf_density(r->basis, *r->scf);
     if (rc == HF_OK && !tuned) {
-      rc = mj->tune(kc);
-      for (int c = 0; c < HF_NCLASS; ++c) grid_scale[c] = mj->grid_scale[c];
-      tuned = true;
+      rc = mj->tune_step(kc);       // the first rounds double as autotuner trials
+      if (mj->tuned) {
+        for (int c = 0; c < HF_NCLASS; ++c) grid_scale[c] = mj->grid_scale[c];
+        tuned = true;
+      }
+    } else if (rc == HF_OK) {
+      rc = mj->launch(kc);
     }
-    if (rc == HF_OK) rc = mj->launch(kc);
     for (size_t i = 0; i < active.size() && rc == HF_OK; ++i) {
       active[i]->scf->quartets += mj->mol_quartets[i];
       rc = scf_post_jk(active[i]->basis, *active[i]->scf);
