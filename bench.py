@@ -270,6 +270,30 @@ def run_ours(args):
     clk = clocks.stop()
     prof = np.mean(np.array(prof), axis=0)
 
+    # production precision modes on the same workload, each timed the same way
+    # and compared with the FP64 build: F = 2J - K
+    F64 = 2.0 * J - K
+    modes = {}
+    for name, o in (("df64", hf.jk_opts(schwarz_tau=WORKLOAD["tau"], df64=True)),
+                    ("fp32_split", hf.jk_opts(schwarz_tau=WORKLOAD["tau"], fp32_bound=1e-5)),
+                    ("fp32_split_df64", hf.jk_opts(schwarz_tau=WORKLOAD["tau"], fp32_bound=1e-5, df64=True)),
+                    ("fp32_split_df64_fp32boys", hf.jk_opts(schwarz_tau=WORKLOAD["tau"], fp32_bound=1e-5,
+                                                            df64=True, fp32_boys=True))):
+        Jm = torch.empty_like(D)
+        Km = torch.empty_like(D)
+        basis.fock_jk(D, Jm, Km, o)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            basis.fock_jk(D, Jm, Km, o)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        modes[name] = {"builds_per_s": 1000.0 / ms, "ms_per_build": ms,
+                       "max_abs_dF_vs_fp64": float((2.0 * Jm - Km - F64).abs().max())}
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     Dh = D.cpu().pin_memory()
     Jh = torch.empty_like(Dh).pin_memory()
@@ -329,6 +353,7 @@ def run_ours(args):
                      "kernel_ms": dom_ms, "kernel_flops": flops[dom],
                      "peak_note": "FP64 CUDA-core nominal: 152 SM x 2 DFMA/clk x 2.07 GHz",
                      "all_classes_tflops": all_flops / (all_ms * 1e-3) / 1e12},
+        "precision_modes": modes,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * n * 8,
                 "d2h_bytes_per_step": 2 * n * n * 8},

@@ -30,6 +30,7 @@ HF_LMAX = 2
 HF_JK_HOST = 1
 HF_JK_DETERMINISTIC = 2
 HF_JK_FP32_BOYS = 4
+HF_JK_DF64 = 8
 HF_SCF_STORED_ERI = 1
 
 

@@ -59,7 +59,7 @@ def hf_scf_opts_default() -> hf_scf_opts:
 
 
 def jk_opts(schwarz_tau: Optional[float] = None, fp32_bound: Optional[float] = None, host: bool = False,
-            fp32_boys: bool = False) -> hf_jk_opts:
+            fp32_boys: bool = False, df64: bool = False) -> hf_jk_opts:
     o = hf_jk_opts_default()
     if schwarz_tau is not None:
         o.schwarz_tau = schwarz_tau
@@ -69,6 +69,8 @@ def jk_opts(schwarz_tau: Optional[float] = None, fp32_bound: Optional[float] = N
         o.flags |= _abi.HF_JK_HOST
     if fp32_boys:
         o.flags |= _abi.HF_JK_FP32_BOYS
+    if df64:
+        o.flags |= _abi.HF_JK_DF64
     return o
 
 
@@ -235,13 +237,13 @@ class Basis:
 
     def scf(self, max_iter: int = 128, e_tol: float = 1e-8, diis_size: int = 8, schwarz_tau: float = 1e-12,
             fp32_bound: float = 0.0, stored_eri: bool = False, D0=None, outputs: bool = True,
-            allow_unconverged: bool = True, fp32_boys: bool = False):
+            allow_unconverged: bool = True, fp32_boys: bool = False, df64: bool = False):
         import torch
         o = hf_scf_opts_default()
         o.max_iter = max_iter
         o.e_tol = e_tol
         o.diis_size = diis_size
-        o.jk = jk_opts(schwarz_tau, fp32_bound, fp32_boys=fp32_boys)
+        o.jk = jk_opts(schwarz_tau, fp32_bound, fp32_boys=fp32_boys, df64=df64)
         if stored_eri:
             o.flags |= _abi.HF_SCF_STORED_ERI
         if D0 is not None:
@@ -281,7 +283,8 @@ class SCFResult:
     tensors: dict
 
 
-def scf_solve_batch(bases, max_iter=128, e_tol=1e-8, diis_size=8, schwarz_tau=1e-12, fp32_bound=0.0):
+def scf_solve_batch(bases, max_iter=128, e_tol=1e-8, diis_size=8, schwarz_tau=1e-12, fp32_bound=0.0,
+                    df64=False):
     """hf_scf_solve_batch over Basis objects sharing one context; returns (results, status)."""
     lib = _lib()
     n = len(bases)
@@ -290,7 +293,7 @@ def scf_solve_batch(bases, max_iter=128, e_tol=1e-8, diis_size=8, schwarz_tau=1e
     o.max_iter = max_iter
     o.e_tol = e_tol
     o.diis_size = diis_size
-    o.jk = jk_opts(schwarz_tau, fp32_bound)
+    o.jk = jk_opts(schwarz_tau, fp32_bound, df64=df64)
     res = (hf_scf_result * n)()
     st = (C.c_int * n)()
     rc = lib.hf_scf_solve_batch(arr, n, C.byref(o), res, st)
@@ -302,7 +305,7 @@ class Server:
     """hf_server: continuous-batching SCF serving loop on a context."""
 
     def __init__(self, ctx: Context, max_active: int = 64, queue_capacity: int = 100000, hbm_budget: int = 0,
-                 max_iter=128, e_tol=1e-8, diis_size=8, schwarz_tau=1e-12, fp32_bound=0.0):
+                 max_iter=128, e_tol=1e-8, diis_size=8, schwarz_tau=1e-12, fp32_bound=0.0, df64=False):
         lib = _lib()
         o = hf_serve_opts()
         lib.hf_serve_opts_default(C.byref(o))
@@ -312,7 +315,7 @@ class Server:
         o.scf.max_iter = max_iter
         o.scf.e_tol = e_tol
         o.scf.diis_size = diis_size
-        o.scf.jk = jk_opts(schwarz_tau, fp32_bound)
+        o.scf.jk = jk_opts(schwarz_tau, fp32_bound, df64=df64)
         self._h = C.c_void_p()
         _check(lib.hf_serve_create(ctx.handle, C.byref(o), C.byref(self._h)), "hf_serve_create")
         self.ctx = ctx

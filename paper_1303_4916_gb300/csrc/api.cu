@@ -125,7 +125,33 @@ int hf_boys_tables(hf_ctx* ctx) {
       }
     }
   }
+  // df64 table: grid T_i = i/16, per (order, row) 16 floats of F-coefficients
+  // (c_0..c_4 as hi/lo pairs, c_5..c_7 as floats) and 16 of exp coefficients
+  const size_t ndf = (size_t)(BOYS_LMAX + 1) * BOYSDF_NGRID * BOYSDF_ROW;
+  std::vector<float> tdf(ndf, 0.0f);
+  for (int i = 0; i < BOYSDF_NGRID; ++i) {
+    boys_row((long double)i / 16.0L, F, &et);
+    for (int L = 0; L <= BOYS_LMAX; ++L) {
+      float* r = &tdf[((size_t)L * BOYSDF_NGRID + i) * BOYSDF_ROW];
+      for (int half = 0; half < 2; ++half) {
+        float* q = r + 16 * half;
+        for (int k = 0; k < 8; ++k) {
+          const long double c = (half == 0 ? F[L + k] : et) / fact[k];
+          if (k < 5) {
+            const float h = (float)c;
+            q[2 * k] = h;
+            q[2 * k + 1] = (float)(c - (long double)h);
+          } else {
+            q[10 + (k - 5)] = (float)c;
+          }
+        }
+      }
+    }
+  }
   void* p = nullptr;
+  HF_CHECK(hf_dev_alloc(ctx, &p, ndf * sizeof(float)));
+  ctx->boysdf = (float*)p;
+  HF_CUDA(cudaMemcpyAsync(ctx->boysdf, tdf.data(), ndf * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   HF_CHECK(hf_dev_alloc(ctx, &p, n64 * sizeof(double)));
   ctx->boys64 = (double*)p;
   HF_CHECK(hf_dev_alloc(ctx, &p, n32 * sizeof(float)));
@@ -198,6 +224,7 @@ extern "C" void hf_ctx_destroy(hf_ctx* c) {
   cudaSetDevice(c->device);
   if (c->boys64) hf_dev_free(c, c->boys64, 0);
   if (c->boys32) hf_dev_free(c, c->boys32, 0);
+  if (c->boysdf) hf_dev_free(c, c->boysdf, 0);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->cublas) cublasDestroy(c->cublas);
   if (c->cusolver) cusolverDnDestroy(c->cusolver);

@@ -36,8 +36,8 @@ __global__ void pair_kernel(int npairs, const int* __restrict__ pA, const int* _
                             const int* __restrict__ sh_l, const int* __restrict__ sh_nprim,
                             const int* __restrict__ sh_prim, const int* __restrict__ sh_bf,
                             const double* __restrict__ exps, const double* __restrict__ coefs,
-                            double* __restrict__ prim64, float* __restrict__ prim32, PairInfo* __restrict__ info,
-                            double eps) {
+                            double* __restrict__ prim64, float* __restrict__ prim32, float* __restrict__ primdf,
+                            PairInfo* __restrict__ info, double eps) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= npairs) return;
   const int A = pA[t], B = pB[t];
@@ -83,6 +83,12 @@ __global__ void pair_kernel(int npairs, const int* __restrict__ pA, const int* _
     float* f = prim32 + (size_t)(base + s) * PRIM32_STRIDE;
     for (int x = 0; x < 10; ++x) f[x] = (float)r[x];
     f[10] = 0.f; f[11] = 0.f;
+    float* g = primdf + (size_t)(base + s) * PRIMDF_STRIDE;
+    for (int x = 0; x < 10; ++x) {
+      const float h = __double2float_rn(r[x]);
+      g[2 * x] = h;
+      g[2 * x + 1] = __double2float_rn(r[x] - (double)h);
+    }
   }
   PairInfo pi;
   pi.bfA = sh_bf[A];
@@ -255,7 +261,8 @@ extern "C" int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, con
         (rc = dl.alloc(ctx, nshell)) || (rc = dn.alloc(ctx, nshell)) || (rc = dp.alloc(ctx, nshell)) ||
         (rc = dbf.alloc(ctx, nshell + 1)) || (rc = dxyz.alloc(ctx, 3 * nshell)) || (rc = dexp.alloc(ctx, nprim)) ||
         (rc = dcoef.alloc(ctx, nprim)) || (rc = b->prim64.alloc(ctx, (size_t)off * PRIM64_STRIDE)) ||
-        (rc = b->prim32.alloc(ctx, (size_t)off * PRIM32_STRIDE)) || (rc = b->pinfo.alloc(ctx, np)) ||
+        (rc = b->prim32.alloc(ctx, (size_t)off * PRIM32_STRIDE)) ||
+        (rc = b->primdf.alloc(ctx, (size_t)off * PRIMDF_STRIDE)) || (rc = b->pinfo.alloc(ctx, np)) ||
         (rc = b->Q.alloc(ctx, np)) || (rc = b->ketlist.alloc(ctx, np)) || (rc = b->counters.alloc(ctx, 2 * HF_NCLASS)))
       break;
 #define UP(dst, src, cnt)                                                                                      \
@@ -275,8 +282,8 @@ extern "C" int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, con
     UP(dcoef, b->coefs.data(), nprim);
 #undef UP
     pair_kernel<<<(np + 127) / 128, 128, 0, st>>>(np, dA.ptr, dB.ptr, dOff.ptr, dxyz.ptr, dl.ptr, dn.ptr, dp.ptr, dbf.ptr,
-                                                  dexp.ptr, dcoef.ptr, b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr,
-                                                  kPrimEps);
+                                                  dexp.ptr, dcoef.ptr, b->prim64.ptr, b->prim32.ptr, b->primdf.ptr,
+                                                  b->pinfo.ptr, kPrimEps);
     if (cudaGetLastError() != cudaSuccess) { rc = hf_fail(HF_ERR_CUDA, "pair_kernel launch"); break; }
     // Schwarz factors per pair class, using the (X|X) diagonal quartets.
     DevArray<int> ids;
@@ -287,8 +294,8 @@ extern "C" int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, con
       rc = hf_fail(HF_ERR_CUDA, "upload");
       break;
     }
-    PairSet ps{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
-    KernelCommon kc{ctx->boys64, ctx->boys32, 0};
+    const PairSet ps = hf_pairset(b);
+    const KernelCommon kc = hf_kernel_common(ctx, 0);
     for (int X = 0; X < HF_NPAIRCLASS; ++X) {
       const int n = b->class_begin[X + 1] - b->class_begin[X];
       if (n <= 0) continue;
@@ -350,7 +357,7 @@ extern "C" int hf_basis_nshell(const hf_basis* b) { return b ? b->nshell : 0; }
 
 extern "C" size_t hf_basis_device_bytes(const hf_basis* b) {
   if (!b) return 0;
-  size_t s = b->prim64.bytes() + b->prim32.bytes() + b->pinfo.bytes() + b->Q.bytes() + b->ketlist.bytes() +
+  size_t s = b->prim64.bytes() + b->prim32.bytes() + b->primdf.bytes() + b->pinfo.bytes() + b->Q.bytes() + b->ketlist.bytes() +
              b->counters.bytes() + b->hD.bytes() + b->hJ.bytes() + b->hK.bytes() + b->S.bytes() + b->T.bytes() +
              b->V.bytes();
   for (int c = 0; c < HF_NCLASS; ++c)
@@ -493,8 +500,8 @@ int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const 
   HF_CUDA(cudaMemsetAsync(J, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(K, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(b->counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
-  PairSet ps{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
-  KernelCommon kc{ctx->boys64, ctx->boys32, (o.flags & HF_JK_FP32_BOYS) ? 1 : 0};
+  const PairSet ps = hf_pairset(b);
+  const KernelCommon kc = hf_kernel_common(ctx, o.flags);
   long long total = 0;
   // heaviest classes first
   for (int c = HF_NCLASS - 1; c >= 0; --c) {
@@ -502,7 +509,8 @@ int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const 
     ClassWork& w64 = b->work64[c];
     ClassWork& w32 = b->work32[c];
     const MolJK one{D, J, K, b->nbf, 0};
-    if (w64.w.nitems > 0) op.jk64(w64.w, ps, kc, one, nullptr, launch_grid(ctx, op.occ64(), w64.w.nitems), st);
+    if (w64.w.nitems > 0)
+      hf_jk_hi(op, o.flags)(w64.w, ps, kc, one, nullptr, launch_grid(ctx, hf_occ_hi(op, o.flags), w64.w.nitems), st);
     if (w32.w.nitems > 0) op.jk32(w32.w, ps, kc, one, nullptr, launch_grid(ctx, op.occ32(), w32.w.nitems), st);
     total += w64.nquartets + w32.nquartets;
   }
@@ -578,8 +586,8 @@ extern "C" int hf_fock_jk_profiled(hf_basis* b, const double* D, double* J, doub
   HF_CUDA(cudaMemsetAsync(J, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(K, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(b->counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
-  PairSet ps{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
-  KernelCommon kc{ctx->boys64, ctx->boys32, (o.flags & HF_JK_FP32_BOYS) ? 1 : 0};
+  const PairSet ps = hf_pairset(b);
+  const KernelCommon kc = hf_kernel_common(ctx, o.flags);
   const MolJK one{D, J, K, b->nbf, 0};
   cudaEvent_t ev[2 * HF_NCLASS + 1];
   for (auto& e : ev) HF_CUDA(cudaEventCreate(&e));
@@ -591,8 +599,8 @@ extern "C" int hf_fock_jk_profiled(hf_basis* b, const double* D, double* J, doub
     for (int r = 0; r < 2; ++r) {
       ClassWork& w = r == 0 ? b->work64[c] : b->work32[c];
       if (w.w.nitems <= 0) continue;
-      (r == 0 ? op.jk64 : op.jk32)(w.w, ps, kc, one, nullptr,
-                                   launch_grid(ctx, r == 0 ? op.occ64() : op.occ32(), w.w.nitems), st);
+      (r == 0 ? hf_jk_hi(op, o.flags) : op.jk32)(
+          w.w, ps, kc, one, nullptr, launch_grid(ctx, r == 0 ? hf_occ_hi(op, o.flags) : op.occ32(), w.w.nitems), st);
       which[nev - 1] = 2 * c + r;
       HF_CUDA(cudaEventRecord(ev[nev++], st));
     }
@@ -656,8 +664,8 @@ int hf_eri_tensor_device(hf_basis* b, double* G) {
   cudaStream_t st = ctx->stream;
   HF_CHECK(hf_basis_prepare_work(b, 0.0, 0.0));
   HF_CUDA(cudaMemsetAsync(b->counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
-  PairSet ps{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
-  KernelCommon kc{ctx->boys64, ctx->boys32, 0};
+  const PairSet ps = hf_pairset(b);
+  const KernelCommon kc = hf_kernel_common(ctx, 0);
   for (int c = 0; c < HF_NCLASS; ++c) {
     ClassWork& w = b->work64[c];
     if (w.w.nitems > 0) ctx->ops[c].store(w.w, ps, kc, G, b->nbf, launch_grid(ctx, 4, w.w.nitems), st);

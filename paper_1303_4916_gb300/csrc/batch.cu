@@ -53,9 +53,10 @@ extern "C" int hf_scf_solve_batch(hf_basis* const* bases, int count, const hf_sc
     Kp[i] = S[i]->K.ptr;
   }
   MultiJK mj;
+  mj.jk_flags = o.jk.flags;
   HF_CHECK(mj.build(ctx, mols, Dp, Jp, Kp));
   HF_CHECK(mj.set_active(active));
-  const KernelCommon kc{ctx->boys64, ctx->boys32, (o.jk.flags & HF_JK_FP32_BOYS) ? 1 : 0};
+  const KernelCommon kc = hf_kernel_common(ctx, o.jk.flags);
   bool tuned = false;
   int nactive = 0;
   for (int a : active) nactive += a;

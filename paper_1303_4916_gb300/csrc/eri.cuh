@@ -22,6 +22,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "df64.cuh"
 #include "eri_classes.cuh"
 #include "hf_device.h"
 
@@ -202,6 +205,102 @@ __device__ __forceinline__ void contracted_vrr(const PairSet& ps, const KernelCo
   }
 }
 
+// ------------------------------------------------------------- df64 path
+// Boys in df64: grid T_i = i/16 (exact in FP32), x = T_i - T exact as a
+// two-term sum; F_m(T) = sum_{k<8} F_{m+k}(T_i) x^k/k! by Horner, the
+// terms k >= 5 (below 2^-30 of the sum, |x| <= 1/32) in FP32, k <= 4 in
+// df64.  For L >= 2: F_L that way, exp(-T) likewise, then the downward
+// recursion in df64.  T >= BOYS_TMAX: F_0 = sqrt(pi)/2 T^{-1/2},
+// F_{m+1} = (2m+1)/(2T) F_m.
+__device__ __forceinline__ df64 boys_horner_df(const float* __restrict__ c, df64 x) {
+  const float4* c4 = reinterpret_cast<const float4*>(c);
+  const float4 q0 = __ldg(c4), q1 = __ldg(c4 + 1), q2 = __ldg(c4 + 2), q3 = __ldg(c4 + 3);
+  float g = __fmaf_rn(q3.x, x.hi, q2.w);  // c7 x + c6
+  g = __fmaf_rn(g, x.hi, q2.z);           // + c5
+  df64 f = df64(q2.x, q2.y) + df_mulf(x, g);
+  f = df64(q1.z, q1.w) + x * f;
+  f = df64(q1.x, q1.y) + x * f;
+  f = df64(q0.z, q0.w) + x * f;
+  return df64(q0.x, q0.y) + x * f;
+}
+
+// (hi, lo) of 1/(2m+1), m = 0..7
+__device__ __forceinline__ df64 df_inv_odd(int m) {
+  constexpr double v[8] = {1.0, 1.0 / 3, 1.0 / 5, 1.0 / 7, 1.0 / 9, 1.0 / 11, 1.0 / 13, 1.0 / 15};
+  const float h = (float)v[m];
+  return df64(h, (float)(v[m] - (double)h));
+}
+
+template <int L>
+__device__ __forceinline__ void boys_df(df64 T, const float* __restrict__ tab, df64* F) {
+  if (T.hi < (float)BOYS_TMAX) {
+    const int i = __float2int_rn(T.hi * BOYSDF_INV_H);
+    const float xh = __fsub_rn((float)i * (1.0f / BOYSDF_INV_H), T.hi);  // exact (Sterbenz)
+    const df64 x = df64(xh, 0.0f) + df64(-T.lo, 0.0f);
+    if (L <= 1) {
+#pragma unroll
+      for (int m = 0; m <= L; ++m) F[m] = boys_horner_df(tab + ((size_t)m * BOYSDF_NGRID + i) * BOYSDF_ROW, x);
+    } else {
+      const float* __restrict__ r = tab + ((size_t)L * BOYSDF_NGRID + i) * BOYSDF_ROW;
+      F[L] = boys_horner_df(r, x);
+      const df64 e = boys_horner_df(r + 16, x);
+      const df64 t2 = df_scale2(T, 2.0f);
+#pragma unroll
+      for (int m = L - 1; m >= 0; --m) F[m] = (t2 * F[m + 1] + e) * df_inv_odd(m);
+    }
+  } else {
+    const df64 rt = rsqrt(T);
+    const df64 o2t = df_scale2(rt * rt, 0.5f);
+    constexpr double kHalfSqrtPi = 0.88622692545275801365;
+    F[0] = rt * df64((float)kHalfSqrtPi, (float)(kHalfSqrtPi - (double)(float)kHalfSqrtPi));
+#pragma unroll
+    for (int m = 0; m < L; ++m) F[m + 1] = df_mulf(F[m] * o2t, (float)(2 * m + 1));
+  }
+}
+
+__device__ __forceinline__ void load_prim_df(const float* __restrict__ base, int idx, Prim<df64>& q) {
+  const float4* s = reinterpret_cast<const float4*>(base + (size_t)idx * PRIMDF_STRIDE);
+  const float4 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2), d = __ldg(s + 3), e = __ldg(s + 4);
+  q.p = df64(a.x, a.y); q.o2p = df64(a.z, a.w);
+  q.P[0] = df64(b.x, b.y); q.P[1] = df64(b.z, b.w); q.P[2] = df64(c.x, c.y);
+  q.PA[0] = df64(c.z, c.w); q.PA[1] = df64(d.x, d.y); q.PA[2] = df64(d.z, d.w);
+  q.K = df64(e.x, e.y);
+}
+
+template <class C>
+__device__ __forceinline__ void contracted_vrr_df(const PairSet& ps, const KernelCommon& kc, int b0, int nb, int k0,
+                                                  int nk, df64* acc) {
+#pragma unroll
+  for (int x = 0; x < C::NE * C::NF; ++x) acc[x] = df64(0.0f, 0.0f);
+  for (int ib = 0; ib < nb; ++ib) {
+    Prim<df64> a;
+    load_prim_df(ps.primdf, b0 + ib, a);
+    for (int ik = 0; ik < nk; ++ik) {
+      Prim<df64> c;
+      load_prim_df(ps.primdf, k0 + ik, c);
+      const df64 pq = a.p + c.p;
+      const df64 rs = rsqrt(pq);
+      const df64 inv = rs * rs;
+      const df64 rp = c.p * inv;  // rho / zeta
+      const df64 rq = a.p * inv;  // rho / eta
+      df64 PQ[3], WP[3], WQ[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        PQ[i] = a.P[i] - c.P[i];
+        WP[i] = -(rp * PQ[i]);
+        WQ[i] = rq * PQ[i];
+      }
+      const df64 T = a.p * rp * (PQ[0] * PQ[0] + PQ[1] * PQ[1] + PQ[2] * PQ[2]);
+      df64 B[C::L + 1];
+      boys_df<C::L>(T, kc.boysdf, B);
+      const df64 pref = a.K * c.K * rs;
+#pragma unroll
+      for (int m = 0; m <= C::L; ++m) B[m] = B[m] * pref;
+      C::template vrr<df64>(acc, B, a.PA, WP, c.PA, WQ, a.o2p, c.o2p, df_scale2(inv, 0.5f), rp, rq);
+    }
+  }
+}
+
 // Cartesian component scale of a d function relative to the axial one
 // (xy, xz, yz carry sqrt(3)); s and p components are 1.
 __device__ __forceinline__ constexpr double comp_scale(int l, int c) {
@@ -248,7 +347,10 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
     const PairInfo ket = P.info[kp];
 
     R acc[C::NE * C::NF];
-    contracted_vrr<C, R>(P, kc, bra.prim0, bra.nprim, ket.prim0, active ? ket.nprim : 0, acc);
+    if constexpr (std::is_same<R, df64>::value)
+      contracted_vrr_df<C>(P, kc, bra.prim0, bra.nprim, ket.prim0, active ? ket.nprim : 0, acc);
+    else
+      contracted_vrr<C, R>(P, kc, bra.prim0, bra.nprim, ket.prim0, active ? ket.nprim : 0, acc);
     R I[NA * NB * NC * ND];
     {
       R AB[3] = {(R)bra.AB[0], (R)bra.AB[1], (R)bra.AB[2]};
@@ -463,6 +565,21 @@ __global__ void __launch_bounds__(128) eri_schwarz_kernel(const int* __restrict_
                                 const MolJK* mols, int grid, cudaStream_t s) {                           \
     hfk::eri_jk_kernel<hfgen::CLS, float><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                    \
   }                                                                                                      \
+  static void launch_jkdf_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one, \
+                                const MolJK* mols, int grid, cudaStream_t s) {                           \
+    if constexpr (hfgen::CLS::L <= HF_DF_LMAX)                                                           \
+      hfk::eri_jk_kernel<hfgen::CLS, df64><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                   \
+    else                                                                                                 \
+      hfk::eri_jk_kernel<hfgen::CLS, double><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                 \
+  }                                                                                                      \
+  static int occ_jkdf_##CLS() {                                                                          \
+    int n = 0;                                                                                           \
+    if constexpr (hfgen::CLS::L <= HF_DF_LMAX)                                                           \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hfk::eri_jk_kernel<hfgen::CLS, df64>, 128, 0);   \
+    else                                                                                                 \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hfk::eri_jk_kernel<hfgen::CLS, double>, 128, 0); \
+    return n;                                                                                            \
+  }                                                                                                      \
   static void launch_store_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, double* G,   \
                                  int nbf, int grid, cudaStream_t s) {                                    \
     hfk::eri_store_kernel<hfgen::CLS><<<grid, 128, 0, s>>>(w, ps, kc, G, nbf);                           \
@@ -488,6 +605,8 @@ __global__ void __launch_bounds__(128) eri_schwarz_kernel(const int* __restrict_
     EriClassOps& e = table[class_index(la, lb, lc, ld)];                                                 \
     e.jk64 = launch_jk64_##CLS;                                                                          \
     e.jk32 = launch_jk32_##CLS;                                                                          \
+    e.jkdf = launch_jkdf_##CLS;                                                                          \
+    e.occdf = occ_jkdf_##CLS;                                                                            \
     e.store = launch_store_##CLS;                                                                        \
     e.schwarz = launch_schwarz_##CLS;                                                                    \
     e.occ64 = occ_jk64_##CLS;                                                                            \

@@ -57,6 +57,11 @@ def add(v, i, k):
     return tuple(w)
 
 
+def coef(k, name):
+    """k * name as a source expression (k = 1 needs no multiplication)."""
+    return name if k == 1 else f"((R){k} * {name})"
+
+
 def pick_axis(v):
     # the axis with the largest power; ties broken towards x
     best = 0
@@ -107,12 +112,12 @@ class VRR:
             nflop = 3
             if f1[i] > 0:
                 f2 = add(f1, i, -1)
-                terms.append(f"(R){f1[i]} * o2q * ({self.get(e, f2, m)} - rq * {self.get(e, f2, m + 1)})")
-                nflop += 4
+                terms.append(f"{coef(f1[i], 'o2q')} * ({self.get(e, f2, m)} - rq * {self.get(e, f2, m + 1)})")
+                nflop += 4 if f1[i] > 1 else 3
             if e[i] > 0:
                 e1 = add(e, i, -1)
-                terms.append(f"(R){e[i]} * o2pq * {self.get(e1, f1, m + 1)}")
-                nflop += 3
+                terms.append(f"{coef(e[i], 'o2pq')} * {self.get(e1, f1, m + 1)}")
+                nflop += 3 if e[i] > 1 else 2
         else:
             i = pick_axis(e)
             e1 = add(e, i, -1)
@@ -121,8 +126,8 @@ class VRR:
             nflop = 3
             if e1[i] > 0:
                 e2 = add(e1, i, -1)
-                terms.append(f"(R){e1[i]} * o2p * ({self.get(e2, f, m)} - rp * {self.get(e2, f, m + 1)})")
-                nflop += 4
+                terms.append(f"{coef(e1[i], 'o2p')} * ({self.get(e2, f, m)} - rp * {self.get(e2, f, m + 1)})")
+                nflop += 4 if e1[i] > 1 else 3
         name = f"v{self.nvar}"
         self.nvar += 1
         self.lines.append(f"const R {name} = {' + '.join(terms)};")

@@ -18,14 +18,25 @@
 #define BOYS64_ROW 16
 #define BOYS32_TERMS 5
 #define BOYS32_ROW 10
+// df64 table: grid T_i = i / 16 (exact in FP32), T < BOYS_TMAX; per row and
+// order 32 floats: Taylor coefficients c_k = F_{L+k}(T_i)/k!, k = 0..4 as
+// (hi, lo) pairs then k = 5..7 as floats, pad to 16; the same for exp(-T).
+#define BOYSDF_INV_H 16.0f
+#define BOYSDF_NGRID 962
+#define BOYSDF_ROW 32
+// classes with L = la+lb+lc+ld up to this run in df64 when requested; higher
+// ones keep FP64
+#define HF_DF_LMAX 4
 
 // Primitive-pair record, FP64: p, 1/(2p), P[3], PA[3], K, pad (80 bytes);
-// FP32: the same nine values then three pads (48 bytes).
+// FP32: the same nine values then three pads (48 bytes); df64: the nine
+// values as (hi, lo) float pairs then one pad pair (80 bytes).
 // K = c_a c_b exp(-ab/p |AB|^2) sqrt(2) pi^(5/4) / p, so that the
 // primitive-quartet prefactor 2 pi^(5/2) / (p q sqrt(p+q)) K_ab K_cd of
 // [00|00]^(m) is K_ab' K_cd' / sqrt(p+q).
 #define PRIM64_STRIDE 10
 #define PRIM32_STRIDE 12
+#define PRIMDF_STRIDE 20
 
 // Shell pair (A, B) with l_A >= l_B: first basis functions of A and B,
 // offset and count of its significant primitive pairs (sorted by
@@ -40,6 +51,7 @@ struct PairSet {
   const double* prim64;
   const float* prim32;
   const PairInfo* info;
+  const float* primdf;
 };
 
 #define HF_NPAIRCLASS 6
@@ -63,6 +75,7 @@ struct KernelCommon {
   const double* boys64;
   const float* boys32;
   int boys_fp32;  // evaluate F_m in FP32 for reduced-precision quartets
+  const float* boysdf;
 };
 
 // Work list of one (class, precision) launch.  Entry e pairs bra pair
@@ -96,10 +109,12 @@ typedef int (*occ_fn)();
 struct EriClassOps {
   jk_launch_fn jk64;
   jk_launch_fn jk32;
+  jk_launch_fn jkdf;  // df64 variant (FP64 kernel for classes above HF_DF_LMAX)
   store_launch_fn store;
   schwarz_launch_fn schwarz;
   occ_fn occ64;
   occ_fn occ32;
+  occ_fn occdf;
   int vrr_flops;  // per primitive quartet, as generated
   int hrr_flops;  // per contracted quartet
   const char* name;

@@ -37,6 +37,7 @@ struct hf_ctx {
   int num_sms = 0;
   double* boys64 = nullptr;
   float* boys32 = nullptr;
+  float* boysdf = nullptr;
   EriClassOps ops[HF_NCLASS] = {};
   std::atomic<int> fail_countdown{0};
   std::atomic<long long> device_bytes{0};
@@ -95,6 +96,7 @@ struct hf_basis {
   int class_begin[HF_NPAIRCLASS + 1] = {};
   DevArray<double> prim64;
   DevArray<float> prim32;
+  DevArray<float> primdf;
   DevArray<PairInfo> pinfo;
   DevArray<double> Q;                 // per pair
   std::vector<double> Q_h;
@@ -118,6 +120,20 @@ struct hf_basis {
 };
 
 int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound);
+
+inline PairSet hf_pairset(const hf_basis* b) {
+  return PairSet{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr, b->primdf.ptr};
+}
+inline KernelCommon hf_kernel_common(const hf_ctx* c, unsigned jk_flags) {
+  return KernelCommon{c->boys64, c->boys32, (jk_flags & HF_JK_FP32_BOYS) ? 1 : 0, c->boysdf};
+}
+// launcher for the higher-precision work of a class: df64 when requested
+inline jk_launch_fn hf_jk_hi(const EriClassOps& op, unsigned jk_flags) {
+  return (jk_flags & HF_JK_DF64) ? op.jkdf : op.jk64;
+}
+inline int hf_occ_hi(const EriClassOps& op, unsigned jk_flags) {
+  return (jk_flags & HF_JK_DF64) ? op.occdf() : op.occ64();
+}
 int hf_basis_one_electron(hf_basis* b);  // fills b->S, T, V
 int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts& o,
                       long long* nquartets);

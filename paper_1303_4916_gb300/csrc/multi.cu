@@ -52,7 +52,7 @@ int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vec
     t.K = K[m];
     t.nbf = b->nbf;
     t.active = 1;
-    t.ps = PairSet{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
+    t.ps = hf_pairset(b);
     t.ketlist = b->ketlist.ptr;
     for (int y = 0; y < HF_NPAIRCLASS; ++y) t.ket_off[y] = b->class_begin[y];
   }
@@ -124,7 +124,7 @@ int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
   const dim3 g(std::max(1, 2 * ctx->num_sms / std::max(1, nmol)), nmol);
   zero_jk_batch<<<g, 256, 0, st>>>(table.ptr);
   HF_CUDA(cudaMemsetAsync(counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
-  const PairSet none{nullptr, nullptr, nullptr};
+  const PairSet none{nullptr, nullptr, nullptr, nullptr};
   const MolJK one{};
   cudaEvent_t ev[2] = {nullptr, nullptr};
   if (class_ms) {
@@ -139,10 +139,10 @@ int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
       const JKWork& wk = w[2 * cls + r];
       if (wk.nitems <= 0) continue;
       any = true;
-      const int occ = std::max(r == 0 ? op.occ64() : op.occ32(), 1);
+      const int occ = std::max(r == 0 ? hf_occ_hi(op, jk_flags) : op.occ32(), 1);
       const int per_sm = grid_scale[cls] > 0 ? std::min(occ, grid_scale[cls]) : occ;
       const int grid = std::max(1, std::min((wk.nitems + 3) / 4, per_sm * ctx->num_sms));
-      (r == 0 ? op.jk64 : op.jk32)(wk, none, kc, one, table.ptr, grid, st);
+      (r == 0 ? hf_jk_hi(op, jk_flags) : op.jk32)(wk, none, kc, one, table.ptr, grid, st);
     }
     if (class_ms && any) {
       HF_CUDA(cudaEventRecord(ev[1], st));
@@ -192,6 +192,7 @@ int MultiJK::capture(const KernelCommon& kc) {
   for (int c = 0; c < HF_NCLASS; ++c) {
     ctx->ops[c].occ64();
     ctx->ops[c].occ32();
+    ctx->ops[c].occdf();
   }
   HF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   const int rc = launch(kc);

@@ -20,6 +20,7 @@ struct MultiJK {
   std::vector<long long> mol_quartets;  // per molecule, all classes
   DevArray<int> counters;
   int grid_scale[HF_NCLASS] = {};       // blocks per SM per class chosen by the tuner (0 = full occupancy)
+  unsigned jk_flags = 0;                // HF_JK_* of the launches (precision tiers)
 
   // mols[i] with density/outputs D[i], J[i], K[i]; every basis must have its
   // work lists prepared for the same options.  Rebuilds all device lists.

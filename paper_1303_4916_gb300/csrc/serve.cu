@@ -104,7 +104,7 @@ void hf_server::retire(Request* r, int status) {
 
 void hf_server::run() {
   cudaSetDevice(ctx->device);
-  const KernelCommon kc{ctx->boys64, ctx->boys32, (opts.scf.jk.flags & HF_JK_FP32_BOYS) ? 1 : 0};
+  const KernelCommon kc = hf_kernel_common(ctx, opts.scf.jk.flags);
   std::unique_ptr<MultiJK> mj;
   bool membership_changed = true;
   for (;;) {
@@ -149,6 +149,7 @@ void hf_server::run() {
     int rc = HF_OK;
     if (membership_changed) {
       mj.reset(new MultiJK());
+      mj->jk_flags = opts.scf.jk.flags;
       std::vector<hf_basis*> mols;
       std::vector<const double*> Dp;
       std::vector<double*> Jp, Kp;

@@ -180,6 +180,38 @@ def test_fp32_split_error_is_bounded(ctx, hf):
         assert dj <= 1e-7 and dk <= 1e-7, (dj, dk)
 
 
+@pytest.mark.parametrize("natom,seed,rules", [(6, 2, "sp"), (3, 3, "spd"), (9, 4, "s")])
+def test_df64_tier_matches_oracle(ctx, hf, natom, seed, rules):
+    """Double-float (FP32-pair) arithmetic for the quartets above the FP32
+    bound: J/K within the FP64 tolerance of the oracle."""
+    mol = lattice_molecule(natom, seed, rules)
+    ob = oracle.Basis(mol)
+    D = _density(ob.nbf, seed)
+    J0, K0, _ = ob.jk(D, tau=1e-12, nthreads=oracle.oracle_threads())
+    basis = hf.Basis(ctx, mol)
+    for fb in (0.0, 1e-5):
+        J, K = basis.fock_jk(_t(D), opts=hf.jk_opts(fp32_bound=fb, df64=True))
+        tol = JK_TOL if fb == 0.0 else 1e-7
+        assert np.abs(J.cpu().numpy() - J0).max() <= tol
+        assert np.abs(K.cpu().numpy() - K0).max() <= tol
+
+
+def test_df64_full_size_and_scf(ctx, hf):
+    """40-atom workload: df64 J/K against the FP64 path; SCF energies with
+    df64 against FP64 and the oracle-pinned small case."""
+    mol = lattice_molecule(40, 1, "sp")
+    basis = hf.Basis(ctx, mol)
+    D = _t(_density(basis.nbf, 5, nocc=mol.n_electrons // 2))
+    J64, K64 = basis.fock_jk(D)
+    Jd, Kd = basis.fock_jk(D, opts=hf.jk_opts(df64=True))
+    assert float((Jd - J64).abs().max()) <= JK_TOL
+    assert float((Kd - K64).abs().max()) <= JK_TOL
+    small = lattice_molecule(6, 32, "sp")
+    ro = oracle.rhf(small, max_iter=128, e_tol=1e-8, diis_size=8, tau=1e-12, nthreads=oracle.oracle_threads())
+    r = hf.Basis(ctx, small).scf(max_iter=128, e_tol=1e-8, diis_size=8, df64=True)
+    assert abs(r.energy - ro.energy) <= E_TOL
+
+
 def test_errors(ctx, hf):
     mol = lattice_molecule(3, 1, "sp")
     with pytest.raises(hf.HFError) as e:
