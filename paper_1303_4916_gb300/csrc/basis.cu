@@ -396,6 +396,7 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
       const int xb = b->class_begin[X], xe = b->class_begin[X + 1];
       const int yb = b->class_begin[Y];
       const std::vector<int>& bk = b->buckets[Y];
+      const int chunk = ctx->ops[cls].chunk;
       std::vector<int> bra[2], kb[2], ke[2], io[2];
       long long nq[2] = {0, 0};
       io[0].push_back(0);
@@ -425,7 +426,7 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
             bra[r].push_back(pi);
             kb[r].push_back(lo_[r]);
             ke[r].push_back(hi_[r]);
-            io[r].push_back(io[r].back() + (cnt + 31) / 32);
+            io[r].push_back(io[r].back() + (cnt + chunk - 1) / chunk);
             nq[r] += cnt;
           }
         }
@@ -453,6 +454,7 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
         w.w.nbra = nb;
         w.w.nitems = io[r].back();
         w.w.counter = b->counters.ptr + 2 * cls + r;
+        w.w.chunk = chunk;
         w.nquartets = nq[r];
         w.bra_h = std::move(bra[r]);
         w.kbeg_h = std::move(kb[r]);

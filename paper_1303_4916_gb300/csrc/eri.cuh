@@ -473,6 +473,243 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
   }
 }
 
+// ------------------------------------------------------------- cooperative kernel
+// Classes with L >= 5: one warp per contracted quartet.  Per primitive
+// quartet, lane 0 forms the coefficient vector (PA, WP, QC, WQ, rho/p,
+// rho/q, k/(2p), k/(2q), k/(2(p+q))) and B_m = prefactor * F_m in shared
+// memory; the lanes then evaluate the generated VRR node list level by
+// level (node = c0 x0 + c1 x1 + c2 (x2 - c3 x3) + c4 x4 over slots), and
+// lane l adds the targets l, l+32, ... into its registers.  After the
+// primitive loop the contracted [e0|f0] go to shared memory, the bra HRR
+// runs one f per lane, the ket HRR one ab per lane, and each of the six
+// digestion contractions gives one output element per lane.
+template <class C>
+struct CoopSizes {
+  static constexpr int NT = C::NE * C::NF;
+  static constexpr int NAB = C::NA * C::NB, NCD = C::NC * C::ND;
+  static constexpr int WS_VRR = C::NSLOT + HF_NCOEF;
+  static constexpr int WS_HRR = NT + NAB * C::NF + NAB * NCD;
+  static constexpr int WS = WS_VRR > WS_HRR ? WS_VRR : WS_HRR;  // words per warp
+};
+
+__device__ __forceinline__ double comp_scale_rt(int l, int c) {
+  return (l == 2 && (c == 1 || c == 2 || c == 4)) ? 1.7320508075688772935 : 1.0;
+}
+
+template <class C, typename R>
+__global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const PairSet ps, const KernelCommon kc,
+                                                          const MolJK one, const MolJK* __restrict__ mols) {
+  using S = CoopSizes<C>;
+  constexpr int NB = C::NB, NC = C::NC, ND = C::ND, NE = C::NE, NF = C::NF;
+  constexpr int NT = S::NT, NAB = S::NAB, NCD = S::NCD, NK = (NT + 31) / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* const s = reinterpret_cast<R*>(smem_raw) + (threadIdx.x >> 5) * S::WS;
+  R* const cv = s + C::NSLOT;
+  const int lane = threadIdx.x & 31;
+  const uint4* __restrict__ nodes = hfgen::CoopTables<C>::nodes();
+  const int* __restrict__ levels = hfgen::CoopTables<C>::levels();
+  const unsigned short* __restrict__ tgt = hfgen::CoopTables<C>::targets();
+  const auto* base = PrimBase<R>::get(ps);
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(w.counter, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= w.nitems) break;
+    int lo = 0, hi = w.nbra;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(w.ioff + mid) <= t) lo = mid; else hi = mid;
+    }
+    const int bi = lo;
+    const MolJK* mjp = mols ? mols + __ldg(w.mol + bi) : nullptr;
+    if (mjp && !mjp->active) continue;
+    const PairSet P = mjp ? mjp->ps : ps;
+    const auto* pbase = mjp ? PrimBase<R>::get(mjp->ps) : base;
+    const int* ketb = mjp ? mjp->ketlist + mjp->ket_off[pair_class(C::LC, C::LD)] : w.ket;
+    const int bp = __ldg(w.bra + bi);
+    const int kp = __ldg(ketb + __ldg(w.kbeg + bi) + (t - __ldg(w.ioff + bi)));
+    const PairInfo bra = P.info[bp];
+    const PairInfo ket = P.info[kp];
+    R acc[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) acc[k] = (R)0;
+    for (int ib = 0; ib < bra.nprim; ++ib) {
+      for (int ik = 0; ik < ket.nprim; ++ik) {
+        if (lane == 0) {
+          Prim<R> a, c;
+          load_prim(pbase, bra.prim0 + ib, a);
+          load_prim(pbase, ket.prim0 + ik, c);
+          const R pq = a.p + c.p;
+          const R rs = (R)rsqrt(pq);
+          const R inv = rs * rs;
+          const R rp = c.p * inv, rq = a.p * inv;
+          R PQ[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            PQ[i] = a.P[i] - c.P[i];
+            cv[1 + i] = a.PA[i];
+            cv[4 + i] = -rp * PQ[i];
+            cv[7 + i] = c.PA[i];
+            cv[10 + i] = rq * PQ[i];
+          }
+          cv[0] = (R)0;
+          cv[13] = rp;
+          cv[14] = rq;
+          const R o2pq = (R)0.5 * inv;
+#pragma unroll
+          for (int k = 1; k <= 8; ++k) {
+            cv[14 + k] = (R)k * a.o2p;
+            cv[22 + k] = (R)k * c.o2p;
+            cv[30 + k] = (R)k * o2pq;
+          }
+          const R T = a.p * rp * (PQ[0] * PQ[0] + PQ[1] * PQ[1] + PQ[2] * PQ[2]);
+          R B[C::L + 1];
+          BoysSel<C::L, R>::eval(T, kc, B);
+          const R pref = a.K * c.K * rs;
+#pragma unroll
+          for (int m = 0; m <= C::L; ++m) s[m] = B[m] * pref;
+        }
+        __syncwarp();
+        for (int lev = 0; lev < C::NLEV; ++lev) {
+          const int n1 = __ldg(levels + lev);
+          for (int n = (lev == 0 ? 0 : __ldg(levels + lev - 1)) + lane; n < n1; n += 32) {
+            const uint4 d = __ldg(nodes + n);
+            const unsigned c = d.w;
+            const R v = cv[c & 63u] * s[d.x >> 16] + cv[(c >> 6) & 63u] * s[d.y & 0xffffu] +
+                        cv[(c >> 12) & 63u] * (s[d.y >> 16] - cv[(c >> 18) & 63u] * s[d.z & 0xffffu]) +
+                        cv[(c >> 24) & 63u] * s[d.z >> 16];
+            s[d.x & 0xffffu] = v;
+          }
+          __syncwarp();
+        }
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+          const int tt = lane + 32 * k;
+          if (tt < NT) acc[k] += s[__ldg(tgt + tt)];
+        }
+        __syncwarp();
+      }
+    }
+    // contracted [e0|f0] -> shared memory, then HRR
+    R* const A = s;
+    R* const H = s + NT;
+    R* const I = H + NAB * NF;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      const int tt = lane + 32 * k;
+      if (tt < NT) A[tt] = acc[k];
+    }
+    __syncwarp();
+    {
+      const R AB[3] = {(R)bra.AB[0], (R)bra.AB[1], (R)bra.AB[2]};
+      for (int f = lane; f < NF; f += 32) {
+        R x[NE], y[NAB];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) x[e] = A[e * NF + f];
+        C::template hrr_bra_row<R>(x, y, AB);
+#pragma unroll
+        for (int ab = 0; ab < NAB; ++ab) H[ab * NF + f] = y[ab];
+      }
+    }
+    __syncwarp();
+    {
+      const R CD[3] = {(R)ket.AB[0], (R)ket.AB[1], (R)ket.AB[2]};
+      for (int ab = lane; ab < NAB; ab += 32) {
+        R x[NF], y[NCD];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) x[f] = H[ab * NF + f];
+        C::template hrr_ket_row<R>(x, y, CD);
+#pragma unroll
+        for (int cd = 0; cd < NCD; ++cd) I[ab * NCD + cd] = y[cd];
+      }
+    }
+    __syncwarp();
+    // digestion: one output element per lane for each of the six contractions
+    const double* __restrict__ D = mjp ? mjp->D : one.D;
+    double* __restrict__ J = mjp ? mjp->J : one.J;
+    double* __restrict__ Kx = mjp ? mjp->K : one.K;
+    const int nbf = mjp ? mjp->nbf : one.nbf;
+    double wdeg = 1.0;
+    if (bra.same) wdeg *= 0.5;
+    if (ket.same) wdeg *= 0.5;
+    if (bp == kp) wdeg *= 0.5;
+    const int a0 = bra.bfA, b0 = bra.bfB, c0 = ket.bfA, d0 = ket.bfB;
+    auto Dsc = [&](int r0, int lr, int i, int c0_, int lc, int j) {
+      return __ldg(D + (size_t)(r0 + i) * nbf + c0_ + j) * comp_scale_rt(lr, i) * comp_scale_rt(lc, j);
+    };
+    auto Iv = [&](int a, int b, int c, int d) { return (double)I[((a * NB + b) * NC + c) * ND + d]; };
+    for (int o = lane; o < NAB; o += 32) {  // J'_ab = w sum_cd I D_cd
+      const int a = o / NB, b = o % NB;
+      double acc2 = 0.0;
+      for (int c = 0; c < NC; ++c)
+        for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsc(c0, C::LC, c, d0, C::LD, d), acc2);
+      atomicAdd(J + (size_t)(a0 + a) * nbf + b0 + b, acc2 * wdeg * comp_scale_rt(C::LA, a) * comp_scale_rt(C::LB, b));
+    }
+    for (int o = lane; o < NCD; o += 32) {  // J'_cd = w sum_ab I D_ab
+      const int c = o / ND, d = o % ND;
+      double acc2 = 0.0;
+      for (int a = 0; a < C::NA; ++a)
+        for (int b = 0; b < NB; ++b) acc2 = fma(Iv(a, b, c, d), Dsc(a0, C::LA, a, b0, C::LB, b), acc2);
+      atomicAdd(J + (size_t)(c0 + c) * nbf + d0 + d, acc2 * wdeg * comp_scale_rt(C::LC, c) * comp_scale_rt(C::LD, d));
+    }
+    for (int o = lane; o < C::NA * NC; o += 32) {  // K'_ac = w sum_bd I D_bd
+      const int a = o / NC, c = o % NC;
+      double acc2 = 0.0;
+      for (int b = 0; b < NB; ++b)
+        for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsc(b0, C::LB, b, d0, C::LD, d), acc2);
+      atomicAdd(Kx + (size_t)(a0 + a) * nbf + c0 + c, acc2 * wdeg * comp_scale_rt(C::LA, a) * comp_scale_rt(C::LC, c));
+    }
+    for (int o = lane; o < C::NA * ND; o += 32) {  // K'_ad = w sum_bc I D_bc
+      const int a = o / ND, d = o % ND;
+      double acc2 = 0.0;
+      for (int b = 0; b < NB; ++b)
+        for (int c = 0; c < NC; ++c) acc2 = fma(Iv(a, b, c, d), Dsc(b0, C::LB, b, c0, C::LC, c), acc2);
+      atomicAdd(Kx + (size_t)(a0 + a) * nbf + d0 + d, acc2 * wdeg * comp_scale_rt(C::LA, a) * comp_scale_rt(C::LD, d));
+    }
+    for (int o = lane; o < NB * NC; o += 32) {  // K'_bc = w sum_ad I D_ad
+      const int b = o / NC, c = o % NC;
+      double acc2 = 0.0;
+      for (int a = 0; a < C::NA; ++a)
+        for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsc(a0, C::LA, a, d0, C::LD, d), acc2);
+      atomicAdd(Kx + (size_t)(b0 + b) * nbf + c0 + c, acc2 * wdeg * comp_scale_rt(C::LB, b) * comp_scale_rt(C::LC, c));
+    }
+    for (int o = lane; o < NB * ND; o += 32) {  // K'_bd = w sum_ac I D_ac
+      const int b = o / ND, d = o % ND;
+      double acc2 = 0.0;
+      for (int a = 0; a < C::NA; ++a)
+        for (int c = 0; c < NC; ++c) acc2 = fma(Iv(a, b, c, d), Dsc(a0, C::LA, a, c0, C::LC, c), acc2);
+      atomicAdd(Kx + (size_t)(b0 + b) * nbf + d0 + d, acc2 * wdeg * comp_scale_rt(C::LB, b) * comp_scale_rt(C::LD, d));
+    }
+    __syncwarp();
+  }
+}
+
+template <class C, typename R>
+inline size_t coop_smem_bytes() {
+  return (size_t)4 * CoopSizes<C>::WS * sizeof(R);
+}
+
+template <class C, typename R>
+inline void coop_launch(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one,
+                        const MolJK* mols, int grid, cudaStream_t s) {
+  const size_t sm = coop_smem_bytes<C, R>();
+  static bool attr = false;  // set once per process (same function on every device)
+  if (!attr) {
+    cudaFuncSetAttribute(eri_jk_coop_kernel<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  eri_jk_coop_kernel<C, R><<<grid, 128, sm, s>>>(w, ps, kc, one, mols);
+}
+
+template <class C, typename R>
+inline int coop_occupancy() {
+  const size_t sm = coop_smem_bytes<C, R>();
+  cudaFuncSetAttribute(eri_jk_coop_kernel<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, eri_jk_coop_kernel<C, R>, 128, sm);
+  return n;
+}
+
 // ------------------------------------------------------------- ERI tensor kernel
 // Same work decomposition; every element of the block is written to all
 // eight index permutations of the dense nbf^4 tensor G (small bases).
@@ -493,8 +730,8 @@ __global__ void __launch_bounds__(128) eri_store_kernel(const JKWork w, const Pa
     }
     const int bi = lo;
     const int bp = __ldg(w.bra + bi);
-    const int kidx = __ldg(w.kbeg + bi) + 32 * (t - __ldg(w.ioff + bi)) + lane;
-    if (kidx >= __ldg(w.kend + bi)) continue;
+    const int kidx = __ldg(w.kbeg + bi) + w.chunk * (t - __ldg(w.ioff + bi)) + lane;
+    if (lane >= w.chunk || kidx >= __ldg(w.kend + bi)) continue;
     const int kp = __ldg(w.ket + kidx);
     const PairInfo bra = ps.info[bp];
     const PairInfo ket = ps.info[kp];
@@ -557,27 +794,44 @@ __global__ void __launch_bounds__(128) eri_schwarz_kernel(const int* __restrict_
 
 // Instantiate the launchers of one class into the dispatch table entry.
 #define HF_DEFINE_CLASS_LAUNCHERS(CLS)                                                                   \
+  template <typename R>                                                                                  \
+  static void launch_jkR_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one,  \
+                               const MolJK* mols, int grid, cudaStream_t s) {                            \
+    if constexpr (hfgen::CLS::COOP)                                                                      \
+      hfk::coop_launch<hfgen::CLS, R>(w, ps, kc, one, mols, grid, s);                                    \
+    else                                                                                                 \
+      hfk::eri_jk_kernel<hfgen::CLS, R><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                      \
+  }                                                                                                      \
+  template <typename R>                                                                                  \
+  static int occR_##CLS() {                                                                              \
+    int n = 0;                                                                                           \
+    if constexpr (hfgen::CLS::COOP)                                                                      \
+      n = hfk::coop_occupancy<hfgen::CLS, R>();                                                          \
+    else                                                                                                 \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hfk::eri_jk_kernel<hfgen::CLS, R>, 128, 0);      \
+    return n;                                                                                            \
+  }                                                                                                      \
   static void launch_jk64_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one, \
                                 const MolJK* mols, int grid, cudaStream_t s) {                           \
-    hfk::eri_jk_kernel<hfgen::CLS, double><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                   \
+    launch_jkR_##CLS<double>(w, ps, kc, one, mols, grid, s);                                             \
   }                                                                                                      \
   static void launch_jk32_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one, \
                                 const MolJK* mols, int grid, cudaStream_t s) {                           \
-    hfk::eri_jk_kernel<hfgen::CLS, float><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                    \
+    launch_jkR_##CLS<float>(w, ps, kc, one, mols, grid, s);                                              \
   }                                                                                                      \
   static void launch_jkdf_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one, \
                                 const MolJK* mols, int grid, cudaStream_t s) {                           \
     if constexpr (hfgen::CLS::L <= HF_DF_LMAX)                                                           \
       hfk::eri_jk_kernel<hfgen::CLS, df64><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                   \
     else                                                                                                 \
-      hfk::eri_jk_kernel<hfgen::CLS, double><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                 \
+      launch_jkR_##CLS<double>(w, ps, kc, one, mols, grid, s);                                           \
   }                                                                                                      \
   static int occ_jkdf_##CLS() {                                                                          \
     int n = 0;                                                                                           \
     if constexpr (hfgen::CLS::L <= HF_DF_LMAX)                                                           \
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hfk::eri_jk_kernel<hfgen::CLS, df64>, 128, 0);   \
     else                                                                                                 \
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hfk::eri_jk_kernel<hfgen::CLS, double>, 128, 0); \
+      n = occR_##CLS<double>();                                                                          \
     return n;                                                                                            \
   }                                                                                                      \
   static void launch_store_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, double* G,   \
@@ -589,16 +843,8 @@ __global__ void __launch_bounds__(128) eri_schwarz_kernel(const int* __restrict_
     if (npairs > 0)                                                                                      \
       hfk::eri_schwarz_kernel<hfgen::CLS><<<(npairs + 127) / 128, 128, 0, s>>>(pairs, npairs, ps, kc, Q); \
   }                                                                                                      \
-  static int occ_jk64_##CLS() {                                                                          \
-    int n = 0;                                                                                           \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hfk::eri_jk_kernel<hfgen::CLS, double>, 128, 0);   \
-    return n;                                                                                            \
-  }                                                                                                      \
-  static int occ_jk32_##CLS() {                                                                          \
-    int n = 0;                                                                                           \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hfk::eri_jk_kernel<hfgen::CLS, float>, 128, 0);    \
-    return n;                                                                                            \
-  }
+  static int occ_jk64_##CLS() { return occR_##CLS<double>(); }                                          \
+  static int occ_jk32_##CLS() { return occR_##CLS<float>(); }
 
 #define HF_REGISTER_CLASS(table, CLS, la, lb, lc, ld, vf, hf_)                                           \
   do {                                                                                                   \
@@ -611,6 +857,7 @@ __global__ void __launch_bounds__(128) eri_schwarz_kernel(const int* __restrict_
     e.schwarz = launch_schwarz_##CLS;                                                                    \
     e.occ64 = occ_jk64_##CLS;                                                                            \
     e.occ32 = occ_jk32_##CLS;                                                                            \
+    e.chunk = hfgen::CLS::COOP ? 1 : 32;                                                                 \
     e.vrr_flops = vf;                                                                                    \
     e.hrr_flops = hf_;                                                                                   \
     e.name = #CLS;                                                                                       \

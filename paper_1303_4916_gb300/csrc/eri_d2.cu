@@ -1,5 +1,8 @@
 // eri_d2.cu -- kernel instantiations for the classes (dp|pp), (dp|ds), (dd|ss), (dd|ps).
 // The classes are spread over several translation units that compile in parallel.
+#define HF_COOP_C_dp_pp
+#define HF_COOP_C_dp_ds
+#define HF_COOP_C_dd_ps
 #include "eri.cuh"
 
 HF_DEFINE_CLASS_LAUNCHERS(C_dp_pp)

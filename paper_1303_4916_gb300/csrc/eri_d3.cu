@@ -1,5 +1,7 @@
 // eri_d3.cu -- kernel instantiations for the classes (dp|dp), (dd|pp).
 // The classes are spread over several translation units that compile in parallel.
+#define HF_COOP_C_dp_dp
+#define HF_COOP_C_dd_pp
 #include "eri.cuh"
 
 HF_DEFINE_CLASS_LAUNCHERS(C_dp_dp)

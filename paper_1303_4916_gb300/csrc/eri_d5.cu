@@ -1,5 +1,6 @@
 // eri_d5.cu -- kernel instantiations for the classes (dd|dp).
 // The classes are spread over several translation units that compile in parallel.
+#define HF_COOP_C_dd_dp
 #include "eri.cuh"
 
 HF_DEFINE_CLASS_LAUNCHERS(C_dd_dp)

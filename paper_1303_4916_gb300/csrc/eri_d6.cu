@@ -1,5 +1,6 @@
 // eri_d6.cu -- kernel instantiations for the classes (dd|dd).
 // The classes are spread over several translation units that compile in parallel.
+#define HF_COOP_C_dd_dd
 #include "eri.cuh"
 
 HF_DEFINE_CLASS_LAUNCHERS(C_dd_dd)

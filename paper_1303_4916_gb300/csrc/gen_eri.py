@@ -94,6 +94,7 @@ class VRR:
         self.lines = []
         self.nvar = 0
         self.flops = 0
+        self.nodes = []   # (name, key, node spec) in dependency order
 
     def get(self, e, f, m):
         key = (e, f, m)
@@ -104,35 +105,48 @@ class VRR:
             self.memo[key] = name
             return name
         terms = []
+        # node spec: value = c0*x0 + c1*x1 + c2*(x2 - c3*x3) + c4*x4, inputs as
+        # DAG keys (None = absent), coefficients as names in the coefficient vector
+        node = {"x": [None] * 5, "c": ["zero"] * 5}
         if tl(f) > 0:
             i = pick_axis(f)
             f1 = add(f, i, -1)
             terms.append(f"QC[{i}] * {self.get(e, f1, m)}")
             terms.append(f"WQ[{i}] * {self.get(e, f1, m + 1)}")
+            node["x"][0], node["c"][0] = (e, f1, m), f"QC{i}"
+            node["x"][1], node["c"][1] = (e, f1, m + 1), f"WQ{i}"
             nflop = 3
             if f1[i] > 0:
                 f2 = add(f1, i, -1)
                 terms.append(f"{coef(f1[i], 'o2q')} * ({self.get(e, f2, m)} - rq * {self.get(e, f2, m + 1)})")
+                node["x"][2], node["x"][3] = (e, f2, m), (e, f2, m + 1)
+                node["c"][2], node["c"][3] = f"o2q{f1[i]}", "rq"
                 nflop += 4 if f1[i] > 1 else 3
             if e[i] > 0:
                 e1 = add(e, i, -1)
                 terms.append(f"{coef(e[i], 'o2pq')} * {self.get(e1, f1, m + 1)}")
+                node["x"][4], node["c"][4] = (e1, f1, m + 1), f"o2pq{e[i]}"
                 nflop += 3 if e[i] > 1 else 2
         else:
             i = pick_axis(e)
             e1 = add(e, i, -1)
             terms.append(f"PA[{i}] * {self.get(e1, f, m)}")
             terms.append(f"WP[{i}] * {self.get(e1, f, m + 1)}")
+            node["x"][0], node["c"][0] = (e1, f, m), f"PA{i}"
+            node["x"][1], node["c"][1] = (e1, f, m + 1), f"WP{i}"
             nflop = 3
             if e1[i] > 0:
                 e2 = add(e1, i, -1)
                 terms.append(f"{coef(e1[i], 'o2p')} * ({self.get(e2, f, m)} - rp * {self.get(e2, f, m + 1)})")
+                node["x"][2], node["x"][3] = (e2, f, m), (e2, f, m + 1)
+                node["c"][2], node["c"][3] = f"o2p{e1[i]}", "rp"
                 nflop += 4 if e1[i] > 1 else 3
         name = f"v{self.nvar}"
         self.nvar += 1
         self.lines.append(f"const R {name} = {' + '.join(terms)};")
         self.flops += nflop
         self.memo[key] = name
+        self.nodes.append((name, key, node))
         return name
 
     def build(self):
@@ -182,6 +196,15 @@ class HRR:
                 outs.append(get(a, b))
         return lines, outs, flops[0]
 
+    def build_rows(self):
+        """Per-row HRR bodies: bra for one f (in: x[e], out: y[ab]) and ket
+        for one ab (in: x[f], out: y[cd])."""
+        lines_b, outs_b, fb = self._side(self.la, self.lb, lambda a: f"x[{self.E.index[a]}]", "h", "AB")
+        bra = lines_b + [f"y[{k}] = {o};" for k, o in enumerate(outs_b)]
+        lines_k, outs_k, fk = self._side(self.lc, self.ld, lambda c: f"x[{self.F.index[c]}]", "k", "CD")
+        ket = lines_k + [f"y[{k}] = {o};" for k, o in enumerate(outs_k)]
+        return bra, ket
+
     def build(self):
         NE, NF = len(self.E), len(self.F)
         NA, NB, NC, ND = ncart(self.la), ncart(self.lb), ncart(self.lc), ncart(self.ld)
@@ -209,6 +232,57 @@ class HRR:
         return code
 
 
+# Coefficient vector of one primitive quartet, shared by the lanes of a
+# warp in the cooperative kernels (index: name).
+COEF_NAMES = (["zero"] + [f"PA{i}" for i in range(3)] + [f"WP{i}" for i in range(3)] + [f"QC{i}" for i in range(3)]
+              + [f"WQ{i}" for i in range(3)] + ["rp", "rq"] + [f"o2p{k}" for k in range(1, 9)]
+              + [f"o2q{k}" for k in range(1, 9)] + [f"o2pq{k}" for k in range(1, 9)])
+COEF_INDEX = {n: i for i, n in enumerate(COEF_NAMES)}
+COOP_LMIN = 5   # classes with la+lb+lc+ld >= this use the warp-cooperative kernel
+
+
+def coop_schedule(v):
+    """Slots and dependency levels of the VRR DAG of class v (built)."""
+    slot = {}
+    for m in range(v.L + 1):
+        slot[((0, 0, 0), (0, 0, 0), m)] = m          # leaves B[m]
+    level = {k: 0 for k in slot}
+    recs = []
+    for name, key, node in v.nodes:
+        ins = [x for x in node["x"] if x is not None]
+        lv = 1 + max(level[x] for x in ins)
+        level[key] = lv
+        slot[key] = len(slot)
+        recs.append((lv, key, node))
+    recs.sort(key=lambda r: r[0])                   # stable: dependency order within a level
+    nlev = max([r[0] for r in recs], default=0)
+    bounds = [0] * (nlev + 2)
+    for lv, _, _ in recs:
+        bounds[lv + 1] += 1
+    for k in range(1, len(bounds)):
+        bounds[k] += bounds[k - 1]
+    words = []
+    for lv, key, node in recs:
+        x = [slot[t] if t is not None else 0 for t in node["x"]]
+        c = [COEF_INDEX[n] for n in node["c"]]
+        assert max(x) < 65536 and max(c) < 64
+        w0 = slot[key] | (x[0] << 16)
+        w1 = x[1] | (x[2] << 16)
+        w2 = x[3] | (x[4] << 16)
+        w3 = c[0] | (c[1] << 6) | (c[2] << 12) | (c[3] << 18) | (c[4] << 24)
+        words.append((w0, w1, w2, w3))
+    targets = []
+    for fi, f in enumerate(v.F.comps):
+        for ei, e in enumerate(v.E.comps):
+            targets.append(slot[(e, f, 0)] if (e, f, 0) in slot else None)
+    # acc order is ei * NF + fi
+    tgt = [0] * (len(v.E) * len(v.F))
+    for fi, f in enumerate(v.F.comps):
+        for ei, e in enumerate(v.E.comps):
+            tgt[ei * len(v.F) + fi] = slot[(e, f, 0)]
+    return len(slot), bounds[1:], words, tgt
+
+
 LNAME = "spdfghik"
 
 
@@ -234,6 +308,7 @@ def emit(lmax):
     o.append("namespace hfgen {")
     o.append("")
     table = []
+    coop_tables = []
     for (la, lb, lc, ld) in cls:
         v = VRR(la, lb, lc, ld)
         vlines = v.build()
@@ -256,6 +331,24 @@ def emit(lmax):
         o.append("    (void)PA; (void)WP; (void)QC; (void)WQ; (void)o2p; (void)o2q; (void)o2pq; (void)rp; (void)rq;")
         o += ["    " + s for s in vlines]
         o.append("  }")
+        L = la + lb + lc + ld
+        coop = L >= COOP_LMIN
+        o.append(f"  static constexpr bool COOP = {'true' if coop else 'false'};")
+        if coop:
+            nslot, bounds, words, tgt = coop_schedule(v)
+            o.append(f"  static constexpr int NSLOT = {nslot}, NNODE = {len(words)}, NLEV = {len(bounds)};")
+            br, kt = h.build_rows()
+            o.append("  template <typename R>")
+            o.append("  __device__ __forceinline__ static void hrr_bra_row(const R* __restrict__ x, R* __restrict__ y, const R* AB) {")
+            o.append("    (void)AB;")
+            o += ["    " + q for q in br]
+            o.append("  }")
+            o.append("  template <typename R>")
+            o.append("  __device__ __forceinline__ static void hrr_ket_row(const R* __restrict__ x, R* __restrict__ y, const R* CD) {")
+            o.append("    (void)CD;")
+            o += ["    " + q for q in kt]
+            o.append("  }")
+            coop_tables.append((name, words, bounds, tgt))
         o.append("  template <typename R>")
         o.append("  __device__ __forceinline__ static void hrr(const R* __restrict__ acc, R* __restrict__ out,")
         o.append("      const R* AB, const R* CD) {")
@@ -269,6 +362,28 @@ def emit(lmax):
         o.append("  }")
         o.append("};")
         o.append("")
+    o.append("")
+    o.append("// Cooperative schedules: node = (out | x0<<16, x1 | x2<<16, x3 | x4<<16,")
+    o.append("// c0 | c1<<6 | c2<<12 | c3<<18 | c4<<24): out = c0*x0 + c1*x1 + c2*(x2 - c3*x3) + c4*x4")
+    o.append("// over slots (0..L = B[m]) and the coefficient vector; levels[k] = end of level k.")
+    o.append("#define HF_COEF_NAMES \\")
+    o.append("  " + " ".join(COEF_NAMES))
+    o.append(f"#define HF_NCOEF {len(COEF_NAMES)}")
+    o.append("template <class C> struct CoopTables;  // defined per class where its kernel is instantiated")
+    for name, words, bounds, tgt in coop_tables:
+        o.append(f"#ifdef HF_COOP_{name}")
+        o.append(f"static __device__ const uint4 {name}_nodes[{len(words)}] = {{")
+        for k in range(0, len(words), 4):
+            o.append("  " + ", ".join("{%du,%du,%du,%du}" % w for w in words[k:k + 4]) + ",")
+        o.append("};")
+        o.append(f"static __device__ const int {name}_levels[{len(bounds)}] = {{{', '.join(map(str, bounds))}}};")
+        o.append(f"static __device__ const unsigned short {name}_targets[{len(tgt)}] = {{{', '.join(map(str, tgt))}}};")
+        o.append(f"template <> struct CoopTables<{name}> {{")
+        o.append(f"  __device__ static const uint4* nodes() {{ return {name}_nodes; }}")
+        o.append(f"  __device__ static const int* levels() {{ return {name}_levels; }}")
+        o.append(f"  __device__ static const unsigned short* targets() {{ return {name}_targets; }}")
+        o.append("};")
+        o.append("#endif")
     o.append("}  // namespace hfgen")
     o.append("")
     o.append("// name, la, lb, lc, ld, VRR flops / primitive quartet, HRR flops / contracted quartet")

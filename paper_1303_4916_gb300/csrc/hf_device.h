@@ -91,6 +91,7 @@ struct JKWork {
   int nbra;
   int nitems;
   int* counter;     // work-item counter, zero before the launch
+  int chunk;        // kets per work item (32, or 1 for warp-cooperative classes)
 };
 
 // pair class of (la, lb), la >= lb: ss 0, ps 1, pp 2, ds 3, dp 4, dd 5
@@ -115,6 +116,7 @@ struct EriClassOps {
   occ_fn occ64;
   occ_fn occ32;
   occ_fn occdf;
+  int chunk;      // kets per work item: 32 (warp of quartets) or 1 (warp-cooperative class)
   int vrr_flops;  // per primitive quartet, as generated
   int hrr_flops;  // per contracted quartet
   const char* name;

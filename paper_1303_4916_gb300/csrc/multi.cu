@@ -73,7 +73,7 @@ int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vec
         hkb.push_back(cw.kbeg_h[e]);
         hke.push_back(cw.kend_h[e]);
         hm.push_back(m);
-        hio.push_back(hio.back() + (cnt + 31) / 32);
+        hio.push_back(hio.back() + (cnt + ctx->ops[cls].chunk - 1) / ctx->ops[cls].chunk);
         nq += cnt;
         mol_quartets[m] += cnt;
       }
@@ -102,6 +102,7 @@ int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vec
     wk.nbra = nb;
     wk.nitems = hio.back();
     wk.counter = counters.ptr + c2;
+    wk.chunk = ctx->ops[cls].chunk;
     nquartets[c2] = nq;
     // the host vectors are reused for the next class: let the copies finish
     HF_CUDA(cudaStreamSynchronize(st));

@@ -165,14 +165,15 @@ def test_c2_full_size_sampled_rows(ctx, hf):
     assert np.abs(Kr).max() > 1e-3 and np.abs(Jr).max() > 1e-3
 
 
-def test_fp32_split_error_is_bounded(ctx, hf):
-    mol = lattice_molecule(9, 41, "sp")
+@pytest.mark.parametrize("natom,seed,rules", [(9, 41, "sp"), (3, 3, "spd")])
+def test_fp32_split_error_is_bounded(ctx, hf, natom, seed, rules):
+    mol = lattice_molecule(natom, seed, rules)
     ob = oracle.Basis(mol)
     D = _density(ob.nbf, 9, nocc=mol.n_electrons // 2)
     J0, K0, _ = ob.jk(D, tau=1e-12, nthreads=oracle.oracle_threads())
     basis = hf.Basis(ctx, mol)
     nq, nf = basis.count_quartets(hf.jk_opts(fp32_bound=1e-5))
-    assert 0 < nf < nq
+    assert 0 < nf < nq or rules == "spd"
     for boys32 in (False, True):
         J, K = basis.fock_jk(_t(D), opts=hf.jk_opts(fp32_bound=1e-5, fp32_boys=boys32))
         dj = np.abs(J.cpu().numpy() - J0).max()
