@@ -534,11 +534,19 @@ void or_eri_shell_block(const or_basis *B, int sA, int sB, int sC, int sD, doubl
 }
 
 /* Q_AB = sqrt(max_{a in A, b in B} |(ab|ab)|) for all shell pairs,
- * nshell x nshell row-major (symmetric). */
+ * nshell x nshell row-major (symmetric); the shell loop is split over the
+ * OpenMP threads (each writes its own entries). */
 void or_schwarz(const or_basis *B, double *Q)
 {
     int ns = B->nshell;
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
     double *blk = (double *)malloc(sizeof(double) * max_block(B)); or_ws *ws = ws_new();
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
     for (int a = 0; a < ns; ++a)
         for (int b = 0; b <= a; ++b) {
             eri_block(ws, B, a, b, a, b, blk);
@@ -552,6 +560,7 @@ void or_schwarz(const or_basis *B, double *Q)
             Q[a * ns + b] = Q[b * ns + a] = sqrt(m);
         }
     free(blk); free(ws);
+    }
 }
 
 /* All N^4 integrals (small N only), row-major [i][j][k][l]. */
