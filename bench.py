@@ -457,6 +457,57 @@ def run_c3(args):
                       "max_abs_dF_mixed_vs_fp64": dF}), flush=True)
 
 
+def run_c3check(args):
+    """150-atom s+p+d lattice (seed 2), full size: one FP64 J/K build and one
+    FP32-split + df64 build at a density supported on a few shells, timed,
+    compared with each other and with J/K rows from the CPU oracle."""
+    import torch
+    import oracle
+    import paper_1303_4916_gb300 as hf
+    from synth import lattice_molecule
+    mol = lattice_molecule(150, 2, "spd")
+    t0 = time.perf_counter()
+    ctx, basis = _ctx_basis(mol, hf)
+    setup_s = time.perf_counter() - t0
+    ob = oracle.Basis(mol)
+    rng = np.random.default_rng(11)
+    dsh = [s_ for s_ in range(mol.nshell) if mol.shell_l[s_] == 2]
+    shells = sorted(set(rng.choice(mol.nshell, size=4, replace=False).tolist() + [dsh[0], dsh[len(dsh) // 2]]))
+    idx = np.concatenate([np.arange(ob.shell_bf[s_], ob.shell_bf[s_ + 1]) for s_ in shells])
+    C = np.zeros((ob.nbf, 6))
+    C[idx] = rng.normal(size=(idx.size, 6)) / np.sqrt(idx.size)
+    Dn = C @ C.T
+    D = torch.tensor(Dn, device="cuda:0")
+    rows = np.array([int(idx[0]), int(idx[-1]), 0, ob.nbf // 2, ob.nbf - 1])
+    out = {}
+    for name, o in (("fp64", hf.jk_opts(schwarz_tau=1e-12)),
+                    ("fp32_split_df64", hf.jk_opts(schwarz_tau=1e-12, fp32_bound=1e-5, df64=True))):
+        J = torch.empty_like(D)
+        K = torch.empty_like(D)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        basis.fock_jk(D, J, K, o)
+        torch.cuda.synchronize()
+        out[name] = {"seconds_per_build": time.perf_counter() - t0, "J": J.cpu().numpy(), "K": K.cpu().numpy(),
+                     "quartets": basis.count_quartets(o)}
+    t0 = time.perf_counter()
+    Jr, Kr = ob.jk_rows(Dn, rows, tau=1e-12, nthreads=oracle.oracle_threads())
+    t_or = time.perf_counter() - t0
+    res = {}
+    for name, v in out.items():
+        res[name] = {"seconds_per_build": v["seconds_per_build"], "builds_per_s": 1.0 / v["seconds_per_build"],
+                     "quartets_total_fp32": v["quartets"],
+                     "max_abs_dJ_rows_vs_oracle": float(np.abs(v["J"][rows] - Jr).max()),
+                     "max_abs_dK_rows_vs_oracle": float(np.abs(v["K"][rows] - Kr).max())}
+    dF = np.abs((2 * out["fp32_split_df64"]["J"] - out["fp32_split_df64"]["K"]) - (2 * out["fp64"]["J"] - out["fp64"]["K"])).max()
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "value": res["fp32_split_df64"]["builds_per_s"], "dtype": "f64/df64+f32",
+                      "data": "synthetic",
+                      "config": {"workload": f"150-atom s+p+d lattice (seed 2), nbf {basis.nbf}, density on shells {shells}",
+                                 "setup_s": setup_s, "rows": rows.tolist(), "oracle_rows_s": t_or,
+                                 "oracle_threads": oracle.oracle_threads()},
+                      "modes": res, "max_abs_dF_mixed_vs_fp64": float(dF)}), flush=True)
+
+
 def run_batch(args):
     """Batched SCF of the first --nmol molecules of the 512-molecule stream
     (atoms U[4,60], s+p rules, seeds 1000+i) versus a loop of single-molecule
@@ -467,12 +518,12 @@ def run_batch(args):
     ctx = hf.Context(0)
     bases = [hf.Basis(ctx, m) for m in mols]
     t0 = time.perf_counter()
-    plain = [b.scf(max_iter=128, e_tol=1e-8, diis_size=8, outputs=False) for b in bases]
+    plain = [b.scf(max_iter=128, e_tol=args.e_tol, diis_size=8, outputs=False) for b in bases]
     t_plain = time.perf_counter() - t0
     out = {}
-    for name, fb in (("batch_fp64", 0.0), ("batch_mixed", 1e-5)):
+    for name, fb, dfm in (("batch_fp64", 0.0, False), ("batch_mixed", 1e-5, False), ("batch_mixed_df64", 1e-5, True)):
         t0 = time.perf_counter()
-        res, st = hf.scf_solve_batch(bases, max_iter=128, e_tol=1e-8, diis_size=8, fp32_bound=fb)
+        res, st = hf.scf_solve_batch(bases, max_iter=128, e_tol=args.e_tol, diis_size=8, fp32_bound=fb, df64=dfm)
         dt = time.perf_counter() - t0
         builds = sum(r.fock_builds for r in res)
         both = [(r, p) for r, p in zip(res, plain) if r.converged and p.converged]
@@ -482,13 +533,19 @@ def run_batch(args):
                      "n_both_converged": len(both),
                      "n_dE_above_1e-8": int(sum(abs(r.energy - p.energy) > 1e-8 for r, p in both))}
     pb = sum(p.fock_builds for p in plain)
-    line = {"metric": "molecule Fock builds/s", "unit": "builds/s", "value": out["batch_mixed"]["mol_fock_builds_per_s"],
+    res_last = res
+    per_mol = [{"natom": int(m.natom), "nbf": int(b.nbf), "plain_conv": bool(p.converged), "plain_it": int(p.iterations),
+                "batch_conv": bool(r.converged), "batch_it": int(r.iterations), "gap": float(p.homo_lumo_gap),
+                "dE": float(abs(r.energy - p.energy))}
+               for m, b, p, r in zip(mols, bases, plain, res_last)]
+    line = {"metric": "molecule Fock builds/s", "unit": "builds/s", "value": out["batch_mixed_df64"]["mol_fock_builds_per_s"],
             "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": f"first {len(mols)} of 512 molecules, atoms U[4,60], s+p, seeds 1000+i",
+                       "e_tol": args.e_tol,
                        "nbf_total": int(sum(b.nbf for b in bases))},
             "plain_loop": {"seconds": t_plain, "mol_fock_builds_per_s": pb / t_plain, "scf_per_s": len(mols) / t_plain,
                            "converged": int(sum(p.converged for p in plain))},
-            **out}
+            **out, "per_molecule_mixed": per_mol}
     print(json.dumps(line), flush=True)
 
 
@@ -504,7 +561,7 @@ def run_serve(args):
     t_arr, sizes, seeds = serve_stream(args.nreq, atoms=(4, args.atoms_max))
     mols = [lattice_molecule(int(n), int(s), "spd") for n, s in zip(sizes, seeds)]
     ctx = hf.Context(0)
-    srv = hf.Server(ctx, max_active=args.max_active, fp32_bound=1e-5)
+    srv = hf.Server(ctx, max_active=args.max_active, fp32_bound=1e-5, df64=args.df64, e_tol=args.e_tol)
     tickets = [None] * len(mols)
     t_start = time.perf_counter()
 
@@ -519,36 +576,50 @@ def run_serve(args):
     f.join()
     srv.drain(args.serve_timeout)
     wall = time.perf_counter() - t_start
-    lat, builds, energies = [], 0, []
+    lat, builds, energies, conv, its = [], 0, [], [], []
     for t in tickets:
         r = srv.poll(t)
         lat.append(r.t_done - r.t_submit)
         builds += r.fock_builds
         energies.append(r.energy)
+        conv.append(bool(r.converged))
+        its.append(int(r.iterations))
     srv.close()
     # the same stream through the plain FP64 single-molecule path, FIFO
     end = 0.0
-    lat_plain, e_plain = [], []
+    lat_plain, e_plain, conv_plain, gaps = [], [], [], []
     for i, m in enumerate(mols):
         b = hf.Basis(ctx, m)
         t0 = time.perf_counter()
-        r = b.scf(max_iter=128, e_tol=1e-8, diis_size=8, outputs=False)
+        r = b.scf(max_iter=128, e_tol=args.e_tol, diis_size=8, outputs=False)
         dt = time.perf_counter() - t0
         start = max(t_arr[i], end)
         end = start + dt
         lat_plain.append(end - t_arr[i])
         e_plain.append(r.energy)
+        conv_plain.append(bool(r.converged))
+        gaps.append(float(r.homo_lumo_gap))
+    dE = np.abs(np.array(energies) - np.array(e_plain))
+    both = np.array(conv) & np.array(conv_plain)
     q = lambda v, p: float(np.percentile(np.array(v), p))
     print(json.dumps({"metric": "p99 SCF latency", "unit": "s", "value": q(lat, 99), "higher_is_better": False,
                       "dtype": "f64+f32", "data": "synthetic",
                       "config": {"workload": f"first {len(mols)} requests of the Poisson stream (200/s), atoms "
-                                             f"logU[4,{args.atoms_max}], s+p+d", "max_active": args.max_active},
+                                             f"logU[4,{args.atoms_max}], s+p+d", "max_active": args.max_active,
+                                 "served_precision": "fp32 split 1e-5" + (" + df64" if args.df64 else ""),
+                                 "e_tol": args.e_tol},
                       "served": {"p50_s": q(lat, 50), "p99_s": q(lat, 99), "solves_per_s": len(mols) / wall,
                                  "fock_builds_per_s": builds / wall,
                                  "offered_per_s": len(mols) / max(t_arr[-1], 1e-9)},
                       "plain_fifo": {"p50_s": q(lat_plain, 50), "p99_s": q(lat_plain, 99),
                                      "solves_per_s": len(mols) / end},
-                      "max_abs_dE_served_vs_plain": float(np.max(np.abs(np.array(energies) - np.array(e_plain))))}),
+                      "n_converged_served": int(sum(conv)), "n_converged_plain": int(sum(conv_plain)),
+                      "n_both_converged": int(both.sum()),
+                      "max_abs_dE_both_converged": float(dE[both].max()) if both.any() else None,
+                      "n_dE_above_1e-8_both_converged": int((dE[both] > 1e-8).sum()),
+                      "per_request": [{"natom": int(m.natom), "conv": c, "conv_plain": cp, "it": k, "gap": g,
+                                       "dE": float(d)} for m, c, cp, k, g, d in
+                                      zip(mols, conv, conv_plain, its, gaps, dE)]}),
           flush=True)
 
 
@@ -590,7 +661,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "batch", "serve", "classes"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c3check", "batch", "serve", "classes"],
                     help="c2 (default) is the benchmark line; the others print secondary measurements")
     ap.add_argument("--nmol", type=int, default=64)
     ap.add_argument("--nreq", type=int, default=100)
@@ -600,13 +671,15 @@ def main():
     ap.add_argument("--c3-max-seconds", type=float, default=120.0)
     ap.add_argument("--natom", type=int, default=12)
     ap.add_argument("--fp32-bound", type=float, default=0.0)
+    ap.add_argument("--e-tol", type=float, default=1e-8)
+    ap.add_argument("--df64", action="store_true", help="serve: df64 tier above the FP32 bound")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "c2":
-        return {"c1": run_c1, "c3": run_c3, "batch": run_batch, "serve": run_serve,
+        return {"c1": run_c1, "c3": run_c3, "c3check": run_c3check, "batch": run_batch, "serve": run_serve,
                 "classes": run_classes}[args.workload](args)
     return run_ours(args)
 

@@ -139,7 +139,7 @@ const char* hf_last_error(void);
 /* Create a context on CUDA device `device`.  hbm_budget (bytes) caps the
  * device memory the serving loop admits work into (0 = 80% of free
  * memory).  cuda_stream is a cudaStream_t to use (NULL = the library
- * creates its own non-blocking stream).  Errors: HF_ERR_INVALID,
+ * creates its own stream, ordered after the legacy default stream).  Errors: HF_ERR_INVALID,
  * HF_ERR_CUDA (no device), HF_ERR_OOM. */
 int hf_ctx_create(hf_ctx** out, int device, size_t hbm_budget, void* cuda_stream);
 void hf_ctx_destroy(hf_ctx* ctx);
@@ -242,7 +242,8 @@ int hf_jk_stored(hf_basis* b, const double* G, const double* D, double* J, doubl
 /* Closed-shell RHF (Szabo-Ostlund procedure; DIIS of Pulay): Loewdin
  * X = S^{-1/2}, core guess, then per iteration diagonalise X^T F X,
  * D = C_occ C_occ^T, J/K of D, F = H + 2J - K, E = Tr[D(H+F)] + E_nuc,
- * DIIS with error F D S - S D F, until |dE| <= e_tol.
+ * DIIS with error F D S - S D F, until |dE| <= e_tol.  The J/K phase of an
+ * iteration is captured once into a CUDA graph and replayed.
  * Returns HF_ERR_NOT_CONVERGED (result filled) after max_iter,
  * HF_ERR_LINDEP if lambda_min(S) < 1e-10. */
 int hf_scf_solve(hf_basis* b, const hf_scf_opts* opts, hf_scf_result* res);

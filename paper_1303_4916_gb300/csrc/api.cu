@@ -182,7 +182,9 @@ extern "C" int hf_ctx_create(hf_ctx** out, int device, size_t hbm_budget, void* 
     if (cuda_stream) {
       c->stream = (cudaStream_t)cuda_stream;
     } else {
-      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      // a blocking stream: ordered after work on the legacy default stream
+      // (where a caller such as PyTorch may have written the inputs)
+      if (cudaStreamCreate(&c->stream) != cudaSuccess) {
         rc = hf_fail(HF_ERR_CUDA, "cudaStreamCreate");
         break;
       }

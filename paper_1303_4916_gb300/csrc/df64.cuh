@@ -59,6 +59,20 @@ __device__ __forceinline__ df64 df_mulf(df64 a, float b) {
   return df_quick_two_sum(p, e);
 }
 
+// a*b + c with one final normalisation (the product's error term joins the
+// two-sum of the addition)
+__device__ __forceinline__ df64 df_fma(df64 a, df64 b, df64 c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(p, c.hi);
+  const float bb = __fsub_rn(s, p);
+  float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.hi, bb));
+  err = __fadd_rn(err, __fadd_rn(e, c.lo));
+  return df_quick_two_sum(s, err);
+}
+
 // exact scaling by a power of two
 __device__ __forceinline__ df64 df_scale2(df64 a, float pow2) { return df64(a.hi * pow2, a.lo * pow2); }
 

@@ -176,12 +176,14 @@ __device__ __forceinline__ void contracted_vrr(const PairSet& ps, const KernelCo
   const auto* base = PrimBase<R>::get(ps);
 #pragma unroll
   for (int x = 0; x < C::NE * C::NF; ++x) acc[x] = (R)0;
-  for (int ib = 0; ib < nb; ++ib) {
-    Prim<R> a;
-    load_prim(base, b0 + ib, a);
-    for (int ik = 0; ik < nk; ++ik) {
-      Prim<R> c;
-      load_prim(base, k0 + ik, c);
+  // ket primitives outer (a different record per lane, loaded once each),
+  // bra primitives inner (the same record for the whole warp)
+  for (int ik = 0; ik < nk; ++ik) {
+    Prim<R> c;
+    load_prim(base, k0 + ik, c);
+    for (int ib = 0; ib < nb; ++ib) {
+      Prim<R> a;
+      load_prim(base, b0 + ib, a);
       const R pq = a.p + c.p;
       const R rs = (R)rsqrt(pq);
       const R inv = rs * rs;
@@ -209,8 +211,8 @@ __device__ __forceinline__ void contracted_vrr(const PairSet& ps, const KernelCo
 // Boys in df64: grid T_i = i/16 (exact in FP32), x = T_i - T exact as a
 // two-term sum; F_m(T) = sum_{k<8} F_{m+k}(T_i) x^k/k! by Horner, the
 // terms k >= 5 (below 2^-30 of the sum, |x| <= 1/32) in FP32, k <= 4 in
-// df64.  For L >= 2: F_L that way, exp(-T) likewise, then the downward
-// recursion in df64.  T >= BOYS_TMAX: F_0 = sqrt(pi)/2 T^{-1/2},
+// df64.  For L >= 1: F_L that way, exp(-T) likewise (same table row, one
+// cache line), then the downward recursion in df64.  T >= BOYS_TMAX: F_0 = sqrt(pi)/2 T^{-1/2},
 // F_{m+1} = (2m+1)/(2T) F_m.
 __device__ __forceinline__ df64 boys_horner_df(const float* __restrict__ c, df64 x) {
   const float4* c4 = reinterpret_cast<const float4*>(c);
@@ -218,10 +220,10 @@ __device__ __forceinline__ df64 boys_horner_df(const float* __restrict__ c, df64
   float g = __fmaf_rn(q3.x, x.hi, q2.w);  // c7 x + c6
   g = __fmaf_rn(g, x.hi, q2.z);           // + c5
   df64 f = df64(q2.x, q2.y) + df_mulf(x, g);
-  f = df64(q1.z, q1.w) + x * f;
-  f = df64(q1.x, q1.y) + x * f;
-  f = df64(q0.z, q0.w) + x * f;
-  return df64(q0.x, q0.y) + x * f;
+  f = df_fma(x, f, df64(q1.z, q1.w));
+  f = df_fma(x, f, df64(q1.x, q1.y));
+  f = df_fma(x, f, df64(q0.z, q0.w));
+  return df_fma(x, f, df64(q0.x, q0.y));
 }
 
 // (hi, lo) of 1/(2m+1), m = 0..7
@@ -237,10 +239,10 @@ __device__ __forceinline__ void boys_df(df64 T, const float* __restrict__ tab, d
     const int i = __float2int_rn(T.hi * BOYSDF_INV_H);
     const float xh = __fsub_rn((float)i * (1.0f / BOYSDF_INV_H), T.hi);  // exact (Sterbenz)
     const df64 x = df64(xh, 0.0f) + df64(-T.lo, 0.0f);
-    if (L <= 1) {
-#pragma unroll
-      for (int m = 0; m <= L; ++m) F[m] = boys_horner_df(tab + ((size_t)m * BOYSDF_NGRID + i) * BOYSDF_ROW, x);
+    if (L == 0) {
+      F[0] = boys_horner_df(tab + (size_t)i * BOYSDF_ROW, x);
     } else {
+      // one 128-byte row holds both the F_L and the exp coefficients
       const float* __restrict__ r = tab + ((size_t)L * BOYSDF_NGRID + i) * BOYSDF_ROW;
       F[L] = boys_horner_df(r, x);
       const df64 e = boys_horner_df(r + 16, x);
@@ -272,12 +274,12 @@ __device__ __forceinline__ void contracted_vrr_df(const PairSet& ps, const Kerne
                                                   int nk, df64* acc) {
 #pragma unroll
   for (int x = 0; x < C::NE * C::NF; ++x) acc[x] = df64(0.0f, 0.0f);
-  for (int ib = 0; ib < nb; ++ib) {
-    Prim<df64> a;
-    load_prim_df(ps.primdf, b0 + ib, a);
-    for (int ik = 0; ik < nk; ++ik) {
-      Prim<df64> c;
-      load_prim_df(ps.primdf, k0 + ik, c);
+  for (int ik = 0; ik < nk; ++ik) {
+    Prim<df64> c;
+    load_prim_df(ps.primdf, k0 + ik, c);
+    for (int ib = 0; ib < nb; ++ib) {
+      Prim<df64> a;
+      load_prim_df(ps.primdf, b0 + ib, a);
       const df64 pq = a.p + c.p;
       const df64 rs = rsqrt(pq);
       const df64 inv = rs * rs;

@@ -11,6 +11,7 @@
 //   F = sum c_i F_i from [B -1; -1 0][c; lambda] = [0; -1], B_ij = <e_i,e_j>
 //   (oldest pair dropped while cond(B) > 1e14); stop at |E_k - E_{k-1}| <= e_tol.
 //
+// hf_scf_solve replays the J/K phase of each iteration from a CUDA graph.
 // Matrices are symmetric except C and the DIIS products; cuBLAS works
 // column-major, so a row-major symmetric buffer is read as itself.
 #include <algorithm>
@@ -20,6 +21,7 @@
 #include <vector>
 
 #include "hf_internal.h"
+#include "multi.h"
 #include "scf_internal.h"
 
 namespace {
@@ -465,8 +467,27 @@ extern "C" int hf_scf_solve(hf_basis* b, const hf_scf_opts* opts, hf_scf_result*
     HF_CHECK(hf_eri_tensor_device(b, G.ptr));
   }
   HF_CHECK(scf_begin(b, s, o, G.ptr));
+  // Direct J/K: the per-iteration J/K phase (zeroing, one launch per class,
+  // symmetrisation) is captured once into a CUDA graph and replayed.
+  MultiJK mj;
+  const KernelCommon kc = hf_kernel_common(ctx, o.jk.flags);
+  if (!G.ptr) {
+    HF_CHECK(hf_basis_prepare_work(b, o.jk.schwarz_tau, o.jk.fp32_bound));
+    mj.jk_flags = o.jk.flags;
+    HF_CHECK(mj.build(ctx, {b}, {s.D.ptr}, {s.J.ptr}, {s.K.ptr}));
+    HF_CHECK(mj.capture(kc));
+  }
   for (;;) {
-    HF_CHECK(scf_iterate(b, s, o, G.ptr));
+    if (G.ptr) {
+      HF_CHECK(scf_iterate(b, s, o, G.ptr));
+    } else {
+      HF_CHECK(scf_density(b, s));
+      HF_CHECK(mj.run(kc));
+      s.quartets += mj.mol_quartets[0];
+      HF_CHECK(scf_post_jk(b, s));
+      HF_CUDA(cudaStreamSynchronize(ctx->stream));
+      HF_CHECK(scf_diis_step(b, s));
+    }
     if (scf_after_iter(b, s, o)) break;
   }
   HF_CHECK(scf_finish(b, s, res));
