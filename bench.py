@@ -206,6 +206,22 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- multi-rank
+def max_over_ranks(seconds: float, dist=None, device="cpu") -> float:
+    """The job's time is the slowest rank's (replicas, no data-path collective)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps_per_rank: int, seconds_max: float, world: int) -> float:
+    """Whole-job builds/s: the builds of all ranks over the slowest rank's time."""
+    return world * steps_per_rank / seconds_max
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -257,9 +273,7 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = sum(step_ms) / 1000.0
     if dist:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+        total_s = max_over_ranks(total_s, dist, dev)
         dist.barrier()
 
     # per-class kernel durations (CUDA events on the library stream), averaged
@@ -331,7 +345,7 @@ def run_ours(args):
     all_ms = float(prof[:, 0].sum() + prof[:, 1].sum())
     all_flops = sum(flops)
 
-    value = world * args.steps / total_s
+    value = job_value(args.steps, total_s, world)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, nsmp, ntot, dt = oracle_sample_rate(mol, WORKLOAD["tau"], seconds_target=args.cpu_seconds)

@@ -362,3 +362,72 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- C-named entry points
+# One function per C entry point, same name, argument marshalling only.
+
+def hf_ctx_create(device: int = 0, hbm_budget: int = 0, stream=None) -> Context:
+    return Context(device, hbm_budget, stream)
+
+
+def hf_basis_create(ctx: Context, mol, n_electrons: Optional[int] = None) -> Basis:
+    return Basis(ctx, mol, n_electrons)
+
+
+def hf_schwarz(basis: Basis) -> np.ndarray:
+    return basis.schwarz()
+
+
+def hf_count_quartets(basis: Basis, opts: Optional[hf_jk_opts] = None):
+    return basis.count_quartets(opts)
+
+
+def hf_fock_jk(basis: Basis, D, J=None, K=None, opts: Optional[hf_jk_opts] = None):
+    return basis.fock_jk(D, J, K, opts)
+
+
+def hf_fock_jk_noalloc(basis: Basis, D, J, K, opts: Optional[hf_jk_opts] = None):
+    _check(_lib().hf_fock_jk_noalloc(basis.handle, _ptr(D), _ptr(J), _ptr(K), C.byref(opts) if opts else None),
+           "hf_fock_jk_noalloc")
+    return J, K
+
+
+def hf_one_electron(basis: Basis):
+    return basis.one_electron()
+
+
+def hf_eri_tensor(basis: Basis):
+    return basis.eri_tensor()
+
+
+def hf_jk_stored(basis: Basis, G, D):
+    return basis.jk_stored(G, D)
+
+
+def hf_scf_solve(basis: Basis, **kw) -> SCFResult:
+    return basis.scf(**kw)
+
+
+def hf_scf_solve_batch(bases, **kw):
+    return scf_solve_batch(bases, **kw)
+
+
+def hf_serve_create(ctx: Context, **kw) -> Server:
+    return Server(ctx, **kw)
+
+
+def hf_serve_submit(server: Server, mol, n_electrons: Optional[int] = None) -> int:
+    return server.submit(mol, n_electrons)
+
+
+def hf_serve_poll(server: Server, ticket: int):
+    return server.poll(ticket)
+
+
+def hf_serve_cancel(server: Server, ticket: int) -> int:
+    return server.cancel(ticket)
+
+
+def hf_serve_drain(server: Server, timeout_s: float = 600.0):
+    return server.drain(timeout_s)
