@@ -201,6 +201,14 @@ extern "C" int hf_ctx_create(hf_ctx** out, int device, size_t hbm_budget, void* 
       break;
     }
     cusolverDnSetStream(c->cusolver, c->stream);
+    for (int k = 0; k < hf_ctx::kSide && rc == HF_OK; ++k) {
+      if (cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->join_ev[k], cudaEventDisableTiming) != cudaSuccess)
+        rc = hf_fail(HF_ERR_CUDA, "side stream");
+    }
+    if (rc == HF_OK && cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+      rc = hf_fail(HF_ERR_CUDA, "fork event");
+    if (rc != HF_OK) break;
     hf_register_classes_sp(c->ops);
     hf_register_classes_d1(c->ops);
     hf_register_classes_d2(c->ops);
@@ -228,6 +236,11 @@ extern "C" void hf_ctx_destroy(hf_ctx* c) {
   if (c->boys32) hf_dev_free(c, c->boys32, 0);
   if (c->boysdf) hf_dev_free(c, c->boysdf, 0);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int k = 0; k < hf_ctx::kSide; ++k) {
+    if (c->side[k]) cudaStreamDestroy(c->side[k]);
+    if (c->join_ev[k]) cudaEventDestroy(c->join_ev[k]);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->cublas) cublasDestroy(c->cublas);
   if (c->cusolver) cusolverDnDestroy(c->cusolver);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

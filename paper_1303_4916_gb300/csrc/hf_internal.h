@@ -39,6 +39,9 @@ struct hf_ctx {
   float* boys32 = nullptr;
   float* boysdf = nullptr;
   EriClassOps ops[HF_NCLASS] = {};
+  static constexpr int kSide = 4;
+  cudaStream_t side[kSide] = {};     // class launches fork onto these (multi-molecule J/K)
+  cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
   std::atomic<int> fail_countdown{0};
   std::atomic<long long> device_bytes{0};
   std::mutex mu;  // serialises use of the stream-bound library handles

@@ -132,6 +132,15 @@ int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
     HF_CUDA(cudaEventCreate(&ev[0]));
     HF_CUDA(cudaEventCreate(&ev[1]));
   }
+  // Without per-class timing the class launches fork onto the side streams
+  // (round robin, heaviest first) and join before the symmetrisation; the
+  // classes share nothing but the J/K atomics, so they may run concurrently.
+  const bool fork = class_ms == nullptr;
+  if (fork) {
+    HF_CUDA(cudaEventRecord(ctx->fork_ev, st));
+    for (int k = 0; k < hf_ctx::kSide; ++k) HF_CUDA(cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0));
+  }
+  int nlaunch = 0;
   for (int cls = HF_NCLASS - 1; cls >= 0; --cls) {
     const EriClassOps& op = ctx->ops[cls];
     if (class_ms) HF_CUDA(cudaEventRecord(ev[0], st));
@@ -143,7 +152,8 @@ int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
       const int occ = std::max(r == 0 ? hf_occ_hi(op, jk_flags) : op.occ32(), 1);
       const int per_sm = grid_scale[cls] > 0 ? std::min(occ, grid_scale[cls]) : occ;
       const int grid = std::max(1, std::min((wk.nitems + 3) / 4, per_sm * ctx->num_sms));
-      (r == 0 ? hf_jk_hi(op, jk_flags) : op.jk32)(wk, none, kc, one, table.ptr, grid, st);
+      cudaStream_t ls = fork ? ctx->side[nlaunch++ % hf_ctx::kSide] : st;
+      (r == 0 ? hf_jk_hi(op, jk_flags) : op.jk32)(wk, none, kc, one, table.ptr, grid, ls);
     }
     if (class_ms && any) {
       HF_CUDA(cudaEventRecord(ev[1], st));
@@ -158,6 +168,12 @@ int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
     cudaEventDestroy(ev[1]);
   }
   HF_CUDA(cudaGetLastError());
+  if (fork) {
+    for (int k = 0; k < hf_ctx::kSide; ++k) {
+      HF_CUDA(cudaEventRecord(ctx->join_ev[k], ctx->side[k]));
+      HF_CUDA(cudaStreamWaitEvent(st, ctx->join_ev[k], 0));
+    }
+  }
   symmetrize_jk_batch<<<g, 256, 0, st>>>(table.ptr);
   HF_CUDA(cudaGetLastError());
   return HF_OK;
