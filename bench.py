@@ -111,10 +111,22 @@ def fp64_alu_peak(sm_count: int, clock_mhz: float):
 
 
 def kernel_hash():
+    """Hash of the source the dominant kernel, eri_jk_kernel<C_ps_ss, double>,
+    is compiled from: eri.cuh without the cooperative (L >= 5) kernel's
+    section, the generated C_ps_ss class and hf_device.h."""
+    csrc = os.path.join(ROOT, "paper_1303_4916_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("eri.cuh", "eri_classes.cuh", "hf_device.h"):
-        with open(os.path.join(ROOT, "paper_1303_4916_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(csrc, "eri.cuh")) as fh:
+        src = fh.read()
+    a = src.find("// ------------------------------------------------------------- cooperative kernel")
+    b = src.find("// ------------------------------------------------------------- ERI tensor kernel")
+    h.update((src[:a] + src[b:] if 0 <= a < b else src).encode())
+    with open(os.path.join(csrc, "eri_classes.cuh")) as fh:
+        gen = fh.read()
+    i = gen.find("struct C_ps_ss {")
+    h.update(gen[i:gen.find("\n};\n", i)].encode())
+    with open(os.path.join(csrc, "hf_device.h"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -473,26 +485,21 @@ def run_c3(args):
 
 def run_c3check(args):
     """150-atom s+p+d lattice (seed 2), full size: one FP64 J/K build and one
-    FP32-split + df64 build at a density supported on a few shells, timed,
-    compared with each other and with J/K rows from the CPU oracle."""
+    FP32-split + df64 build at a density supported on six shells, timed,
+    compared with each other and with the stored J/K rows of the CPU oracle
+    (tests/golden/c3_rows.npz, written by tests/golden/make_c3_rows.py)."""
     import torch
-    import oracle
     import paper_1303_4916_gb300 as hf
-    from synth import lattice_molecule
+    from synth import lattice_molecule, shell_supported_density
     mol = lattice_molecule(150, 2, "spd")
     t0 = time.perf_counter()
     ctx, basis = _ctx_basis(mol, hf)
     setup_s = time.perf_counter() - t0
-    ob = oracle.Basis(mol)
-    rng = np.random.default_rng(11)
-    dsh = [s_ for s_ in range(mol.nshell) if mol.shell_l[s_] == 2]
-    shells = sorted(set(rng.choice(mol.nshell, size=4, replace=False).tolist() + [dsh[0], dsh[len(dsh) // 2]]))
-    idx = np.concatenate([np.arange(ob.shell_bf[s_], ob.shell_bf[s_ + 1]) for s_ in shells])
-    C = np.zeros((ob.nbf, 6))
-    C[idx] = rng.normal(size=(idx.size, 6)) / np.sqrt(idx.size)
-    Dn = C @ C.T
+    Dn, shells, rows = shell_supported_density(mol, seed=11)
+    gold = np.load(os.path.join(ROOT, "tests", "golden", "c3_rows.npz"))
+    if gold["rows"].tolist() != rows.tolist() or gold["shells"].tolist() != list(shells):
+        raise SystemExit("stored c3 oracle rows were made for another density")
     D = torch.tensor(Dn, device="cuda:0")
-    rows = np.array([int(idx[0]), int(idx[-1]), 0, ob.nbf // 2, ob.nbf - 1])
     out = {}
     for name, o in (("fp64", hf.jk_opts(schwarz_tau=1e-12)),
                     ("fp32_split_df64", hf.jk_opts(schwarz_tau=1e-12, fp32_bound=1e-5, df64=True))):
@@ -504,21 +511,17 @@ def run_c3check(args):
         torch.cuda.synchronize()
         out[name] = {"seconds_per_build": time.perf_counter() - t0, "J": J.cpu().numpy(), "K": K.cpu().numpy(),
                      "quartets": basis.count_quartets(o)}
-    t0 = time.perf_counter()
-    Jr, Kr = ob.jk_rows(Dn, rows, tau=1e-12, nthreads=oracle.oracle_threads())
-    t_or = time.perf_counter() - t0
     res = {}
     for name, v in out.items():
         res[name] = {"seconds_per_build": v["seconds_per_build"], "builds_per_s": 1.0 / v["seconds_per_build"],
                      "quartets_total_fp32": v["quartets"],
-                     "max_abs_dJ_rows_vs_oracle": float(np.abs(v["J"][rows] - Jr).max()),
-                     "max_abs_dK_rows_vs_oracle": float(np.abs(v["K"][rows] - Kr).max())}
+                     "max_abs_dJ_rows_vs_oracle": float(np.abs(v["J"][rows] - gold["J"]).max()),
+                     "max_abs_dK_rows_vs_oracle": float(np.abs(v["K"][rows] - gold["K"]).max())}
     dF = np.abs((2 * out["fp32_split_df64"]["J"] - out["fp32_split_df64"]["K"]) - (2 * out["fp64"]["J"] - out["fp64"]["K"])).max()
     print(json.dumps({"metric": METRIC, "unit": UNIT, "value": res["fp32_split_df64"]["builds_per_s"], "dtype": "f64/df64+f32",
                       "data": "synthetic",
                       "config": {"workload": f"150-atom s+p+d lattice (seed 2), nbf {basis.nbf}, density on shells {shells}",
-                                 "setup_s": setup_s, "rows": rows.tolist(), "oracle_rows_s": t_or,
-                                 "oracle_threads": oracle.oracle_threads()},
+                                 "setup_s": setup_s, "rows": rows.tolist()},
                       "modes": res, "max_abs_dF_mixed_vs_fp64": float(dF)}), flush=True)
 
 
@@ -535,7 +538,8 @@ def run_batch(args):
     plain = [b.scf(max_iter=128, e_tol=args.e_tol, diis_size=8, outputs=False) for b in bases]
     t_plain = time.perf_counter() - t0
     out = {}
-    for name, fb, dfm in (("batch_fp64", 0.0, False), ("batch_mixed", 1e-5, False), ("batch_mixed_df64", 1e-5, True)):
+    for name, fb, dfm in (("batch_fp64", 0.0, False), ("batch_mixed", 1e-5, False), ("batch_df64", 0.0, True),
+                          ("batch_mixed_df64", 1e-5, True)):
         t0 = time.perf_counter()
         res, st = hf.scf_solve_batch(bases, max_iter=128, e_tol=args.e_tol, diis_size=8, fp32_bound=fb, df64=dfm)
         dt = time.perf_counter() - t0
@@ -575,7 +579,8 @@ def run_serve(args):
     t_arr, sizes, seeds = serve_stream(args.nreq, atoms=(4, args.atoms_max))
     mols = [lattice_molecule(int(n), int(s), "spd") for n, s in zip(sizes, seeds)]
     ctx = hf.Context(0)
-    srv = hf.Server(ctx, max_active=args.max_active, fp32_bound=1e-5, df64=args.df64, e_tol=args.e_tol)
+    fb = 1e-5 if args.fp32_bound == 0.0 and not args.no_fp32_split else args.fp32_bound
+    srv = hf.Server(ctx, max_active=args.max_active, fp32_bound=fb, df64=args.df64, e_tol=args.e_tol)
     tickets = [None] * len(mols)
     t_start = time.perf_counter()
 
@@ -620,7 +625,8 @@ def run_serve(args):
                       "dtype": "f64+f32", "data": "synthetic",
                       "config": {"workload": f"first {len(mols)} requests of the Poisson stream (200/s), atoms "
                                              f"logU[4,{args.atoms_max}], s+p+d", "max_active": args.max_active,
-                                 "served_precision": "fp32 split 1e-5" + (" + df64" if args.df64 else ""),
+                                 "served_precision": (f"fp32 split {fb:g}" if fb > 0 else "no fp32 split")
+                                 + (" + df64" if args.df64 else ""),
                                  "e_tol": args.e_tol},
                       "served": {"p50_s": q(lat, 50), "p99_s": q(lat, 99), "solves_per_s": len(mols) / wall,
                                  "fock_builds_per_s": builds / wall,
@@ -651,7 +657,7 @@ def run_classes(args):
     D = torch.tensor(C @ C.T, device="cuda:0")
     J = torch.empty_like(D)
     K = torch.empty_like(D)
-    o = hf.jk_opts(schwarz_tau=1e-12, fp32_bound=args.fp32_bound)
+    o = hf.jk_opts(schwarz_tau=1e-12, fp32_bound=args.fp32_bound, df64=args.df64)
     basis.fock_jk_profiled(D, J, K, o)
     ms = np.mean([basis.fock_jk_profiled(D, J, K, o) for _ in range(3)], axis=0)
     rows = []
@@ -661,9 +667,11 @@ def run_classes(args):
             if q == 0:
                 continue
             fl = pq * st.prim_flops + q * (st.hrr_flops + st.digest_flops)
-            rows.append({"class": name, "precision": "fp32" if r else "fp64", "quartets": q, "prim_quartets": pq,
+            hi = "df64" if args.df64 and st.la + st.lb + st.lc + st.ld <= 4 else "fp64"
+            rows.append({"class": name, "precision": "fp32" if r else hi, "quartets": q, "prim_quartets": pq,
                          "ms": float(ms[c, r]), "tflops": fl / (ms[c, r] * 1e-3) / 1e12 if ms[c, r] > 0 else None})
     print(json.dumps({"workload": f"{args.natom}-atom s+p+d lattice (seed 3), nbf {n}", "fp32_bound": args.fp32_bound,
+                      "df64": bool(args.df64),
                       "total_ms": float(ms.sum()), "classes": rows}), flush=True)
 
 
@@ -686,7 +694,8 @@ def main():
     ap.add_argument("--natom", type=int, default=12)
     ap.add_argument("--fp32-bound", type=float, default=0.0)
     ap.add_argument("--e-tol", type=float, default=1e-8)
-    ap.add_argument("--df64", action="store_true", help="serve: df64 tier above the FP32 bound")
+    ap.add_argument("--df64", action="store_true", help="serve, batch, classes: df64 tier above the FP32 bound")
+    ap.add_argument("--no-fp32-split", action="store_true", help="serve: no FP32 quartets")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

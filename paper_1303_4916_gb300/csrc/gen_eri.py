@@ -95,6 +95,7 @@ class VRR:
         self.nvar = 0
         self.flops = 0
         self.nodes = []   # (name, key, node spec) in dependency order
+        self.exprs = {}   # name -> right-hand side
 
     def get(self, e, f, m):
         key = (e, f, m)
@@ -144,19 +145,34 @@ class VRR:
         name = f"v{self.nvar}"
         self.nvar += 1
         self.lines.append(f"const R {name} = {' + '.join(terms)};")
+        self.exprs[name] = " + ".join(terms)
         self.flops += nflop
         self.memo[key] = name
         self.nodes.append((name, key, node))
         return name
 
     def build(self):
-        acc_lines = []
+        targets = []
         for fi, f in enumerate(self.F.comps):
             for ei, e in enumerate(self.E.comps):
-                v = self.get(e, f, 0)
-                acc_lines.append(f"acc[{ei * len(self.F) + fi}] += {v};")
+                targets.append((ei * len(self.F) + fi, self.get(e, f, 0)))
+        # a target no other node reads is folded into its accumulation:
+        # acc = acc + t0 + t1 + ..., which contracts into FMAs
+        used = set()
+        for name, key, node in self.nodes:
+            for x in node["x"]:
+                if x is not None:
+                    used.add(self.memo[x])
+        folded = {v for _, v in targets if v in self.exprs and v not in used}
+        lines = [ln for ln in self.lines if ln.split(" = ")[0].split()[-1] not in folded]
+        acc_lines = []
+        for k, v in targets:
+            if v in folded:
+                acc_lines.append(f"acc[{k}] = acc[{k}] + {self.exprs[v]};")
+            else:
+                acc_lines.append(f"acc[{k}] += {v};")
         self.flops += len(acc_lines)
-        return self.lines + acc_lines
+        return lines + acc_lines
 
 
 class HRR:

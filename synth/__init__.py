@@ -14,4 +14,6 @@ from .molecules import (  # noqa: F401
     batch_molecules,
     serve_stream,
     concat_basis,
+    shell_bf_offsets,
+    shell_supported_density,
 )

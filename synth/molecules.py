@@ -233,3 +233,36 @@ def concat_basis(mols: List[Molecule]):
         ao += m.natom
         bo += m.nbf
     return out
+
+
+def shell_bf_offsets(mol: Molecule) -> np.ndarray:
+    """First basis function of each shell (Cartesian: 1, 3, 6 per s, p, d),
+    with a final entry equal to nbf."""
+    l = mol.shell_l.astype(np.int64)
+    return np.concatenate([[0], np.cumsum((l + 1) * (l + 2) // 2)])
+
+
+def shell_supported_density(mol: Molecule, seed: int = 11, n_random: int = 4, n_occ: int = 6):
+    """A symmetric positive semidefinite density C C^T whose support is a few
+    shells: ``n_random`` shells drawn at random plus, when the molecule has d
+    shells, its first d shell and the middle one.  Returns (D, shells, rows)
+    where ``rows`` = [first and last supported function, 0, nbf//2, nbf-1]
+    are the J/K rows a sampled comparison looks at.
+
+    Only the rows of J and K that touch the support need the quartets
+    through those shells, which keeps a CPU comparison at several hundred
+    basis functions to minutes.
+    """
+    rng = np.random.default_rng(seed)
+    dsh = [s for s in range(mol.nshell) if mol.shell_l[s] == 2]
+    pick = rng.choice(mol.nshell, size=n_random, replace=False).tolist()
+    if dsh:
+        pick += [dsh[0], dsh[len(dsh) // 2]]
+    shells = sorted(set(pick))
+    off = shell_bf_offsets(mol)
+    nbf = int(off[-1])
+    idx = np.concatenate([np.arange(off[s], off[s + 1]) for s in shells])
+    C = np.zeros((nbf, n_occ))
+    C[idx] = rng.normal(size=(idx.size, n_occ)) / np.sqrt(idx.size)
+    rows = np.array([int(idx[0]), int(idx[-1]), 0, nbf // 2, nbf - 1])
+    return C @ C.T, shells, rows

@@ -327,3 +327,17 @@ def test_jk_rows_with_zero_density_blocks():
     Jr, Kr = B.jk_rows(D, rows)
     np.testing.assert_allclose(Jr, J, atol=1e-13, rtol=0)
     np.testing.assert_allclose(Kr, K, atol=1e-13, rtol=0)
+
+
+def test_stored_c3_rows_are_consistent():
+    """The stored oracle rows of the 150-atom s+p+d molecule were made for
+    the density the synthetic generator draws now, and they obey the
+    symmetry J_ij = J_ji, K_ij = K_ji wherever two stored rows cross."""
+    from synth import shell_supported_density
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "c3_rows.npz"))
+    mol = lattice_molecule(150, 2, "spd")
+    _, shells, rows = shell_supported_density(mol, seed=11)
+    assert gold["rows"].tolist() == rows.tolist() and gold["shells"].tolist() == list(shells)
+    for M in (gold["J"], gold["K"]):
+        sub = M[:, rows]
+        assert np.abs(sub - sub.T).max() <= 1e-13 * max(1.0, np.abs(M).max())
