@@ -112,21 +112,29 @@ def fp64_alu_peak(sm_count: int, clock_mhz: float):
 
 def kernel_hash():
     """Hash of the source the dominant kernel, eri_jk_kernel<C_ps_ss, double>,
-    is compiled from: eri.cuh without the cooperative (L >= 5) kernel's
-    section, the generated C_ps_ss class and hf_device.h."""
+    is compiled from, with // comments removed: eri.cuh without the
+    cooperative (L >= 5) kernel's section and the launcher macros, the
+    generated C_ps_ss class and hf_device.h."""
+    import re
     csrc = os.path.join(ROOT, "paper_1303_4916_gb300", "csrc")
-    h = hashlib.sha256()
+
+    def code(text):
+        lines = re.sub(r"//[^\n]*", "", text).splitlines()
+        return "\n".join(ln.rstrip() for ln in lines if ln.strip())
     with open(os.path.join(csrc, "eri.cuh")) as fh:
         src = fh.read()
     a = src.find("// ------------------------------------------------------------- cooperative kernel")
     b = src.find("// ------------------------------------------------------------- ERI tensor kernel")
-    h.update((src[:a] + src[b:] if 0 <= a < b else src).encode())
+    c = src.find("// Instantiate the launchers of one class")
+    part = src[:a] + src[b:c] if 0 <= a < b < c else src
     with open(os.path.join(csrc, "eri_classes.cuh")) as fh:
         gen = fh.read()
     i = gen.find("struct C_ps_ss {")
-    h.update(gen[i:gen.find("\n};\n", i)].encode())
-    with open(os.path.join(csrc, "hf_device.h"), "rb") as fh:
-        h.update(fh.read())
+    with open(os.path.join(csrc, "hf_device.h")) as fh:
+        dev = fh.read()
+    h = hashlib.sha256()
+    for t in (part, gen[i:gen.find("\n};\n", i)], dev):
+        h.update(code(t).encode())
     return h.hexdigest()[:16]
 
 
@@ -667,7 +675,7 @@ def run_classes(args):
             if q == 0:
                 continue
             fl = pq * st.prim_flops + q * (st.hrr_flops + st.digest_flops)
-            hi = "df64" if args.df64 and st.la + st.lb + st.lc + st.ld <= 4 else "fp64"
+            hi = "df64" if args.df64 else "fp64"
             rows.append({"class": name, "precision": "fp32" if r else hi, "quartets": q, "prim_quartets": pq,
                          "ms": float(ms[c, r]), "tflops": fl / (ms[c, r] * 1e-3) / 1e12 if ms[c, r] > 0 else None})
     print(json.dumps({"workload": f"{args.natom}-atom s+p+d lattice (seed 3), nbf {n}", "fp32_bound": args.fp32_bound,

@@ -89,8 +89,8 @@ typedef struct {
 #define HF_JK_DETERMINISTIC 2u     /* reserved: accepted, currently same as default order */
 #define HF_JK_FP32_BOYS 4u         /* reduced-precision quartets also evaluate F_m(T) in FP32 */
 #define HF_JK_DF64 8u              /* quartets above fp32_bound run in double-float (FP32-pair)
-                                      arithmetic, ~1e-14 relative, for classes with
-                                      la+lb+lc+ld <= 4; heavier classes stay FP64 */
+                                      arithmetic, ~1e-14 relative, in every class (J/K
+                                      digestion and accumulation stay FP64) */
 typedef struct {
     double schwarz_tau;  /* drop shell quartet iff Q_ab*Q_cd < tau (default 1e-12; 0 keeps all) */
     double fp32_bound;   /* quartets with Q_ab*Q_cd < fp32_bound run in FP32 (default 0 = none) */

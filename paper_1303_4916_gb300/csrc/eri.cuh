@@ -476,11 +476,24 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
 }
 
 // ------------------------------------------------------------- cooperative kernel
-// Classes with L >= 5: one warp per contracted quartet.  Per primitive
-// quartet, lane 0 forms the coefficient vector (PA, WP, QC, WQ, rho/p,
-// rho/q, k/(2p), k/(2q), k/(2(p+q))) and B_m = prefactor * F_m in shared
-// memory; the lanes then evaluate the generated VRR node list level by
-// level (node = c0 x0 + c1 x1 + c2 (x2 - c3 x3) + c4 x4 over slots), and
+// df64 hooks of the generic (cooperative) kernel
+__device__ __forceinline__ void load_prim(const float* __restrict__ base, int idx, Prim<df64>& q) {
+  load_prim_df(base, idx, q);
+}
+template <> struct PrimBase<df64> { static __device__ __forceinline__ const float* get(const PairSet& s) { return s.primdf; } };
+template <int L>
+struct BoysSel<L, df64> {
+  static __device__ __forceinline__ void eval(df64 T, const KernelCommon& kc, df64* F) { boys_df<L>(T, kc.boysdf, F); }
+};
+
+// Classes with L >= 5: one warp per contracted quartet.  The primitive
+// quartets are set up G at a time, one per lane: each lane forms its
+// coefficient vector (PA, WP, QC, WQ, rho/p, rho/q, k/(2p), k/(2q),
+// k/(2(p+q))) and B_m = prefactor * F_m in a row of shared memory.  The
+// warp then takes the rows in order: B_m goes to the first VRR slots, the
+// lanes evaluate the generated VRR node list level by level (node =
+// c0 x0 + c1 x1 [+ c2 (x2 - c3 x3)] [+ c4 x4] over slots, c from the row,
+// the bracketed terms as the node's type bits say), and
 // lane l adds the targets l, l+32, ... into its registers.  After the
 // primitive loop the contracted [e0|f0] go to shared memory, the bra HRR
 // runs one f per lane, the ket HRR one ab per lane, and each of the six
@@ -489,9 +502,14 @@ template <class C>
 struct CoopSizes {
   static constexpr int NT = C::NE * C::NF;
   static constexpr int NAB = C::NA * C::NB, NCD = C::NC * C::ND;
-  static constexpr int WS_VRR = C::NSLOT + HF_NCOEF;
+  static constexpr int ROW = HF_NCOEF + C::L + 1;  // one primitive quartet's coefficients and B_m
   static constexpr int WS_HRR = NT + NAB * C::NF + NAB * NCD;
-  static constexpr int WS = WS_VRR > WS_HRR ? WS_VRR : WS_HRR;  // words per warp
+  __host__ __device__ static constexpr int ws(int g) { return C::NSLOT + g * ROW > WS_HRR ? C::NSLOT + g * ROW : WS_HRR; }  // words per warp
+  // rows set up per pass: one per lane.  Measured on GB300 (60-atom s+p+d
+  // molecule) 32 beats 16 and 8 in every class, (dd|dd) included although
+  // its 124 KB per block then allow one block per SM: the serial part of
+  // a primitive quartet, not occupancy, bounds these kernels.
+  static constexpr int G_DEFAULT = 32;
 };
 
 __device__ __forceinline__ double comp_scale_rt(int l, int c) {
@@ -500,13 +518,14 @@ __device__ __forceinline__ double comp_scale_rt(int l, int c) {
 
 template <class C, typename R>
 __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const PairSet ps, const KernelCommon kc,
-                                                          const MolJK one, const MolJK* __restrict__ mols) {
+                                                          const MolJK one, const MolJK* __restrict__ mols,
+                                                          const int G) {
   using S = CoopSizes<C>;
   constexpr int NB = C::NB, NC = C::NC, ND = C::ND, NE = C::NE, NF = C::NF;
   constexpr int NT = S::NT, NAB = S::NAB, NCD = S::NCD, NK = (NT + 31) / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* const s = reinterpret_cast<R*>(smem_raw) + (threadIdx.x >> 5) * S::WS;
-  R* const cv = s + C::NSLOT;
+  R* const s = reinterpret_cast<R*>(smem_raw) + (threadIdx.x >> 5) * S::ws(G);
+  R* const stage = s + C::NSLOT;
   const int lane = threadIdx.x & 31;
   const uint4* __restrict__ nodes = hfgen::CoopTables<C>::nodes();
   const int* __restrict__ levels = hfgen::CoopTables<C>::levels();
@@ -535,51 +554,59 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
     R acc[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) acc[k] = (R)0;
-    for (int ib = 0; ib < bra.nprim; ++ib) {
-      for (int ik = 0; ik < ket.nprim; ++ik) {
-        if (lane == 0) {
-          Prim<R> a, c;
-          load_prim(pbase, bra.prim0 + ib, a);
-          load_prim(pbase, ket.prim0 + ik, c);
-          const R pq = a.p + c.p;
-          const R rs = (R)rsqrt(pq);
-          const R inv = rs * rs;
-          const R rp = c.p * inv, rq = a.p * inv;
-          R PQ[3];
+    const int nq = bra.nprim * ket.nprim;
+    for (int g0 = 0; g0 < nq; g0 += G) {
+      const int q = g0 + lane;
+      if (lane < G && q < nq) {
+        const int ib = q / ket.nprim, ik = q - ib * ket.nprim;
+        R* const cv = stage + lane * S::ROW;
+        Prim<R> a, c;
+        load_prim(pbase, bra.prim0 + ib, a);
+        load_prim(pbase, ket.prim0 + ik, c);
+        const R pq = a.p + c.p;
+        const R rs = (R)rsqrt(pq);
+        const R inv = rs * rs;
+        const R rp = c.p * inv, rq = a.p * inv;
+        R PQ[3];
 #pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            PQ[i] = a.P[i] - c.P[i];
-            cv[1 + i] = a.PA[i];
-            cv[4 + i] = -rp * PQ[i];
-            cv[7 + i] = c.PA[i];
-            cv[10 + i] = rq * PQ[i];
-          }
-          cv[0] = (R)0;
-          cv[13] = rp;
-          cv[14] = rq;
-          const R o2pq = (R)0.5 * inv;
-#pragma unroll
-          for (int k = 1; k <= 8; ++k) {
-            cv[14 + k] = (R)k * a.o2p;
-            cv[22 + k] = (R)k * c.o2p;
-            cv[30 + k] = (R)k * o2pq;
-          }
-          const R T = a.p * rp * (PQ[0] * PQ[0] + PQ[1] * PQ[1] + PQ[2] * PQ[2]);
-          R B[C::L + 1];
-          BoysSel<C::L, R>::eval(T, kc, B);
-          const R pref = a.K * c.K * rs;
-#pragma unroll
-          for (int m = 0; m <= C::L; ++m) s[m] = B[m] * pref;
+        for (int i = 0; i < 3; ++i) {
+          PQ[i] = a.P[i] - c.P[i];
+          cv[1 + i] = a.PA[i];
+          cv[4 + i] = -rp * PQ[i];
+          cv[7 + i] = c.PA[i];
+          cv[10 + i] = rq * PQ[i];
         }
+        cv[0] = (R)0;
+        cv[13] = rp;
+        cv[14] = rq;
+        const R o2pq = (R)0.5 * inv;
+#pragma unroll
+        for (int k = 1; k <= 8; ++k) {
+          cv[14 + k] = (R)k * a.o2p;
+          cv[22 + k] = (R)k * c.o2p;
+          cv[30 + k] = (R)k * o2pq;
+        }
+        const R T = a.p * rp * (PQ[0] * PQ[0] + PQ[1] * PQ[1] + PQ[2] * PQ[2]);
+        R B[C::L + 1];
+        BoysSel<C::L, R>::eval(T, kc, B);
+        const R pref = a.K * c.K * rs;
+#pragma unroll
+        for (int m = 0; m <= C::L; ++m) cv[HF_NCOEF + m] = B[m] * pref;
+      }
+      __syncwarp();
+      const int ng = min(G, nq - g0);
+      for (int jq = 0; jq < ng; ++jq) {
+        const R* const cv = stage + jq * S::ROW;
+        if (lane <= C::L) s[lane] = cv[HF_NCOEF + lane];
         __syncwarp();
         for (int lev = 0; lev < C::NLEV; ++lev) {
           const int n1 = __ldg(levels + lev);
           for (int n = (lev == 0 ? 0 : __ldg(levels + lev - 1)) + lane; n < n1; n += 32) {
             const uint4 d = __ldg(nodes + n);
             const unsigned c = d.w;
-            const R v = cv[c & 63u] * s[d.x >> 16] + cv[(c >> 6) & 63u] * s[d.y & 0xffffu] +
-                        cv[(c >> 12) & 63u] * (s[d.y >> 16] - cv[(c >> 18) & 63u] * s[d.z & 0xffffu]) +
-                        cv[(c >> 24) & 63u] * s[d.z >> 16];
+            R v = cv[c & 63u] * s[d.x >> 16] + cv[(c >> 6) & 63u] * s[d.y & 0xffffu];
+            if (c & (1u << 30)) v = v + cv[(c >> 12) & 63u] * (s[d.y >> 16] - cv[(c >> 18) & 63u] * s[d.z & 0xffffu]);
+            if (c & (1u << 31)) v = v + cv[(c >> 24) & 63u] * s[d.z >> 16];
             s[d.x & 0xffffu] = v;
           }
           __syncwarp();
@@ -686,26 +713,39 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
   }
 }
 
+// Primitive quartets set up per pass: the class default, or HF_COOP_G
+// (8, 16 or 32) from the environment for tuning.
+template <class C>
+inline int coop_group() {
+  static const int g = [] {
+    const char* e = getenv("HF_COOP_G");
+    const int v = e ? atoi(e) : 0;
+    return (v == 8 || v == 16 || v == 32) ? v : CoopSizes<C>::G_DEFAULT;
+  }();
+  return g;
+}
+
 template <class C, typename R>
-inline size_t coop_smem_bytes() {
-  return (size_t)4 * CoopSizes<C>::WS * sizeof(R);
+inline size_t coop_smem_bytes(int g) {
+  return (size_t)4 * CoopSizes<C>::ws(g) * sizeof(R);
 }
 
 template <class C, typename R>
 inline void coop_launch(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one,
                         const MolJK* mols, int grid, cudaStream_t s) {
-  const size_t sm = coop_smem_bytes<C, R>();
+  const int g = coop_group<C>();
+  const size_t sm = coop_smem_bytes<C, R>(g);
   static bool attr = false;  // set once per process (same function on every device)
   if (!attr) {
     cudaFuncSetAttribute(eri_jk_coop_kernel<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  eri_jk_coop_kernel<C, R><<<grid, 128, sm, s>>>(w, ps, kc, one, mols);
+  eri_jk_coop_kernel<C, R><<<grid, 128, sm, s>>>(w, ps, kc, one, mols, g);
 }
 
 template <class C, typename R>
 inline int coop_occupancy() {
-  const size_t sm = coop_smem_bytes<C, R>();
+  const size_t sm = coop_smem_bytes<C, R>(coop_group<C>());
   cudaFuncSetAttribute(eri_jk_coop_kernel<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, eri_jk_coop_kernel<C, R>, 128, sm);
@@ -823,14 +863,18 @@ __global__ void __launch_bounds__(128) eri_schwarz_kernel(const int* __restrict_
   }                                                                                                      \
   static void launch_jkdf_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one, \
                                 const MolJK* mols, int grid, cudaStream_t s) {                           \
-    if constexpr (hfgen::CLS::L <= HF_DF_LMAX)                                                           \
+    if constexpr (hfgen::CLS::COOP)                                                                      \
+      hfk::coop_launch<hfgen::CLS, df64>(w, ps, kc, one, mols, grid, s);                                 \
+    else if constexpr (hfgen::CLS::L <= HF_DF_LMAX)                                                      \
       hfk::eri_jk_kernel<hfgen::CLS, df64><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                   \
     else                                                                                                 \
       launch_jkR_##CLS<double>(w, ps, kc, one, mols, grid, s);                                           \
   }                                                                                                      \
   static int occ_jkdf_##CLS() {                                                                          \
     int n = 0;                                                                                           \
-    if constexpr (hfgen::CLS::L <= HF_DF_LMAX)                                                           \
+    if constexpr (hfgen::CLS::COOP)                                                                      \
+      n = hfk::coop_occupancy<hfgen::CLS, df64>();                                                       \
+    else if constexpr (hfgen::CLS::L <= HF_DF_LMAX)                                                      \
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hfk::eri_jk_kernel<hfgen::CLS, df64>, 128, 0);   \
     else                                                                                                 \
       n = occR_##CLS<double>();                                                                          \

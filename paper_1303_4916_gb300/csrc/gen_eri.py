@@ -270,7 +270,12 @@ def coop_schedule(v):
         level[key] = lv
         slot[key] = len(slot)
         recs.append((lv, key, node))
-    recs.sort(key=lambda r: r[0])                   # stable: dependency order within a level
+    # level order; inside a level, nodes grouped by which optional terms they
+    # have (type bit 0: the c2 (x2 - c3 x3) term, bit 1: the c4 x4 term), so
+    # that the 32 lanes of a warp mostly take the same branch
+    def ntype(node):
+        return int(node["c"][2] != "zero") | (int(node["c"][4] != "zero") << 1)
+    recs.sort(key=lambda r: (r[0], ntype(r[2])))
     nlev = max([r[0] for r in recs], default=0)
     bounds = [0] * (nlev + 2)
     for lv, _, _ in recs:
@@ -285,7 +290,7 @@ def coop_schedule(v):
         w0 = slot[key] | (x[0] << 16)
         w1 = x[1] | (x[2] << 16)
         w2 = x[3] | (x[4] << 16)
-        w3 = c[0] | (c[1] << 6) | (c[2] << 12) | (c[3] << 18) | (c[4] << 24)
+        w3 = c[0] | (c[1] << 6) | (c[2] << 12) | (c[3] << 18) | (c[4] << 24) | (ntype(node) << 30)
         words.append((w0, w1, w2, w3))
     targets = []
     for fi, f in enumerate(v.F.comps):
@@ -380,7 +385,8 @@ def emit(lmax):
         o.append("")
     o.append("")
     o.append("// Cooperative schedules: node = (out | x0<<16, x1 | x2<<16, x3 | x4<<16,")
-    o.append("// c0 | c1<<6 | c2<<12 | c3<<18 | c4<<24): out = c0*x0 + c1*x1 + c2*(x2 - c3*x3) + c4*x4")
+    o.append("// c0 | c1<<6 | c2<<12 | c3<<18 | c4<<24 | type<<30): out = c0*x0 + c1*x1 + c2*(x2 - c3*x3) + c4*x4,")
+    o.append("// the c2 term present iff type bit 0, the c4 term iff type bit 1")
     o.append("// over slots (0..L = B[m]) and the coefficient vector; levels[k] = end of level k.")
     o.append("#define HF_COEF_NAMES \\")
     o.append("  " + " ".join(COEF_NAMES))

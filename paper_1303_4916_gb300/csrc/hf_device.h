@@ -24,8 +24,9 @@
 #define BOYSDF_INV_H 16.0f
 #define BOYSDF_NGRID 962
 #define BOYSDF_ROW 32
-// classes with L = la+lb+lc+ld up to this run in df64 when requested; higher
-// ones keep FP64
+// thread-per-quartet classes with L = la+lb+lc+ld up to this have a df64
+// variant; the warp-cooperative classes (L >= 5) take df64 through the
+// generic cooperative kernel
 #define HF_DF_LMAX 4
 
 // Primitive-pair record, FP64: p, 1/(2p), P[3], PA[3], K, pad (80 bytes);
@@ -110,7 +111,7 @@ typedef int (*occ_fn)();
 struct EriClassOps {
   jk_launch_fn jk64;
   jk_launch_fn jk32;
-  jk_launch_fn jkdf;  // df64 variant (FP64 kernel for classes above HF_DF_LMAX)
+  jk_launch_fn jkdf;  // df64 variant
   store_launch_fn store;
   schwarz_launch_fn schwarz;
   occ_fn occ64;

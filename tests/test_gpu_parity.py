@@ -215,7 +215,8 @@ def test_fp32_split_error_is_bounded(ctx, hf, natom, seed, rules):
 @pytest.mark.parametrize("natom,seed,rules", [(6, 2, "sp"), (3, 3, "spd"), (9, 4, "s")])
 def test_df64_tier_matches_oracle(ctx, hf, natom, seed, rules):
     """Double-float (FP32-pair) arithmetic for the quartets above the FP32
-    bound: J/K within the FP64 tolerance of the oracle."""
+    bound, in every class (the s+p+d cases reach the warp-cooperative
+    kernels of L >= 5): J/K within the FP64 tolerance of the oracle."""
     mol = lattice_molecule(natom, seed, rules)
     ob = oracle.Basis(mol)
     D = _density(ob.nbf, seed)
@@ -226,6 +227,21 @@ def test_df64_tier_matches_oracle(ctx, hf, natom, seed, rules):
         tol = JK_TOL if fb == 0.0 else 1e-7
         assert np.abs(J.cpu().numpy() - J0).max() <= tol
         assert np.abs(K.cpu().numpy() - K0).max() <= tol
+
+
+def test_df64_cooperative_classes_match_fp64(ctx, hf):
+    """12-atom s+p+d molecule: the df64 form of every class, the
+    warp-cooperative L >= 5 ones included, against the FP64 path (itself
+    oracle-pinned above) within the FP64 J/K tolerance."""
+    mol = lattice_molecule(12, 3, "spd")
+    basis = hf.Basis(ctx, mol)
+    D = _t(_density(basis.nbf, 12, nocc=mol.n_electrons // 2))
+    J64, K64 = basis.fock_jk(D)
+    Jd, Kd = basis.fock_jk(D, opts=hf.jk_opts(df64=True))
+    assert float((Jd - J64).abs().max()) <= JK_TOL
+    assert float((Kd - K64).abs().max()) <= JK_TOL
+    heavy = [st for st in basis.class_stats(hf.jk_opts()) if st.la + st.lb + st.lc + st.ld >= 5]
+    assert sum(st.quartets_fp64 for st in heavy) > 0
 
 
 def test_df64_full_size_and_scf(ctx, hf):
