@@ -12,6 +12,10 @@
   invariance of the energy, idempotency at convergence.
 * J/K from the unique-quartet digestion against the plain contraction of
   the full tensor (a different code path in the oracle).
+* DIIS: the exact root of an affine error map, a null-space least-squares
+  solve of the same constrained minimum; Loewdin: X S X = I.
+* The stored rows of the 150-atom molecule: made for the current input and
+  symmetric where two stored rows cross.
 """
 import json
 import math
@@ -341,3 +345,56 @@ def test_stored_c3_rows_are_consistent():
     for M in (gold["J"], gold["K"]):
         sub = M[:, rows]
         assert np.abs(sub - sub.T).max() <= 1e-13 * max(1.0, np.abs(M).max())
+
+
+def test_diis_recovers_the_root_of_an_affine_error():
+    """Pulay's extrapolation (DIIS, named in the paper's SCF description)
+    minimises |sum_i c_i e_i| subject to sum_i c_i = 1.  When the error is an
+    affine function of F, e(F) = P (F - F*) Q with P, Q invertible, and the
+    stored F_i affinely span the space, that minimum is e = 0 at
+    sum_i c_i F_i = F*: the extrapolation must return F* itself.  A wrong
+    sign, a transposed B matrix or a dropped constraint row fails this."""
+    from oracle.scf import diis_extrapolate
+    rng = np.random.default_rng(5)
+    n = 2
+    Fstar = rng.normal(size=(n, n))
+    P = rng.normal(size=(n, n)) + 3 * np.eye(n)
+    Q = rng.normal(size=(n, n)) + 3 * np.eye(n)
+    Fs = [Fstar + rng.normal(size=(n, n)) for _ in range(n * n + 1)]
+    es = [P @ (F - Fstar) @ Q for F in Fs]
+    assert np.abs(diis_extrapolate(Fs, es) - Fstar).max() < 1e-10
+    # with fewer vectors than the space needs, the result is the affine
+    # combination whose error is smallest: check it against a brute-force
+    # least-squares solve of the same constrained problem
+    Fs3, es3 = Fs[:3], es[:3]
+    E = np.stack([e.ravel() for e in es3], axis=1)           # columns e_i
+    # c = c0 + N t with sum c = 1: c0 = (1,0,0), N spans sum-zero vectors
+    N = np.array([[-1.0, -1.0], [1.0, 0.0], [0.0, 1.0]])
+    t, *_ = np.linalg.lstsq(E @ N, -E[:, 0], rcond=None)
+    c = np.array([1.0, 0.0, 0.0]) + N @ t
+    expect = sum(ci * F for ci, F in zip(c, Fs3))
+    assert np.abs(diis_extrapolate(Fs3, es3) - expect).max() < 1e-10
+
+
+def test_diis_drops_vectors_that_make_b_singular():
+    """Identical error vectors make the DIIS matrix singular; the oldest is
+    dropped until it is not, and one vector alone is returned unchanged."""
+    from oracle.scf import diis_extrapolate
+    F1, F2 = np.eye(2), 2 * np.eye(2)
+    e = np.array([[0.0, 1.0], [-1.0, 0.0]])
+    assert np.array_equal(diis_extrapolate([F1, F2], [e, e]), F2)
+
+
+def test_lowdin_is_the_symmetric_inverse_square_root():
+    """X = S^(-1/2) (Loewdin): X symmetric, X S X = I and X X = S^(-1);
+    near-singular S raises LinearDependence."""
+    from oracle.scf import LinearDependence, lowdin
+    mol = lattice_molecule(3, 3, "spd")
+    S, _, _ = oracle.Basis(mol).one_electron()
+    X = lowdin(S)
+    n = S.shape[0]
+    assert np.abs(X - X.T).max() < 1e-13
+    assert np.abs(X @ S @ X - np.eye(n)).max() < 1e-10
+    assert np.abs(X @ X - np.linalg.inv(S)).max() < 1e-8 * np.abs(np.linalg.inv(S)).max()
+    with pytest.raises(LinearDependence):
+        lowdin(np.array([[1.0, 1.0], [1.0, 1.0 + 1e-13]]))
