@@ -486,6 +486,11 @@ struct BoysSel<L, df64> {
   static __device__ __forceinline__ void eval(df64 T, const KernelCommon& kc, df64* F) { boys_df<L>(T, kc.boysdf, F); }
 };
 
+// a * b + c, fused in each arithmetic type of the cooperative kernel
+__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ df64 fmac(df64 a, df64 b, df64 c) { return df_fma(a, b, c); }
+
 // Classes with L >= 5: one warp per contracted quartet.  The primitive
 // quartets are set up G at a time, one per lane: each lane forms its
 // coefficient vector (PA, WP, QC, WQ, rho/p, rho/q, k/(2p), k/(2q),
@@ -604,9 +609,10 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
           for (int n = (lev == 0 ? 0 : __ldg(levels + lev - 1)) + lane; n < n1; n += 32) {
             const uint4 d = __ldg(nodes + n);
             const unsigned c = d.w;
-            R v = cv[c & 63u] * s[d.x >> 16] + cv[(c >> 6) & 63u] * s[d.y & 0xffffu];
-            if (c & (1u << 30)) v = v + cv[(c >> 12) & 63u] * (s[d.y >> 16] - cv[(c >> 18) & 63u] * s[d.z & 0xffffu]);
-            if (c & (1u << 31)) v = v + cv[(c >> 24) & 63u] * s[d.z >> 16];
+            R v = fmac(cv[(c >> 6) & 63u], s[d.y & 0xffffu], cv[c & 63u] * s[d.x >> 16]);
+            if (c & (1u << 30))
+              v = fmac(cv[(c >> 12) & 63u], fmac(-cv[(c >> 18) & 63u], s[d.z & 0xffffu], s[d.y >> 16]), v);
+            if (c & (1u << 31)) v = fmac(cv[(c >> 24) & 63u], s[d.z >> 16], v);
             s[d.x & 0xffffu] = v;
           }
           __syncwarp();

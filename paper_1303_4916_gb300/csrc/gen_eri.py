@@ -259,23 +259,27 @@ COOP_LMIN = 5   # classes with la+lb+lc+ld >= this use the warp-cooperative kern
 
 def coop_schedule(v):
     """Slots and dependency levels of the VRR DAG of class v (built)."""
-    slot = {}
-    for m in range(v.L + 1):
-        slot[((0, 0, 0), (0, 0, 0), m)] = m          # leaves B[m]
-    level = {k: 0 for k in slot}
+    level = {((0, 0, 0), (0, 0, 0), m): 0 for m in range(v.L + 1)}   # leaves B[m]
     recs = []
     for name, key, node in v.nodes:
         ins = [x for x in node["x"] if x is not None]
         lv = 1 + max(level[x] for x in ins)
         level[key] = lv
-        slot[key] = len(slot)
         recs.append((lv, key, node))
+
     # level order; inside a level, nodes grouped by which optional terms they
     # have (type bit 0: the c2 (x2 - c3 x3) term, bit 1: the c4 x4 term), so
-    # that the 32 lanes of a warp mostly take the same branch
+    # that the 32 lanes of a warp mostly take the same branch, then by their
+    # coefficient indices, so that the lanes of a round mostly read the same
+    # coefficients (shared-memory broadcast instead of bank conflicts)
     def ntype(node):
         return int(node["c"][2] != "zero") | (int(node["c"][4] != "zero") << 1)
-    recs.sort(key=lambda r: (r[0], ntype(r[2])))
+    recs.sort(key=lambda r: (r[0], ntype(r[2]), tuple(COEF_INDEX[n] for n in r[2]["c"])))
+    # slots: leaves first, then the nodes in evaluation order, so that a
+    # round's 32 outputs are consecutive
+    slot = {((0, 0, 0), (0, 0, 0), m): m for m in range(v.L + 1)}
+    for lv, key, node in recs:
+        slot[key] = len(slot)
     nlev = max([r[0] for r in recs], default=0)
     bounds = [0] * (nlev + 2)
     for lv, _, _ in recs:
