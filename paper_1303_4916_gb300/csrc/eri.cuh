@@ -629,6 +629,8 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
     R* const A = s;
     R* const H = s + NT;
     R* const I = H + NAB * NF;
+    constexpr bool kPre = sizeof(R) == sizeof(double);      // R = double or df64
+    double* const Id = reinterpret_cast<double*>(I);        // same storage when kPre
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
       const int tt = lane + 32 * k;
@@ -654,8 +656,17 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
 #pragma unroll
         for (int f = 0; f < NF; ++f) x[f] = H[ab * NF + f];
         C::template hrr_ket_row<R>(x, y, CD);
+        if constexpr (kPre) {
+          // FP64 and df64: stored once as a double, already multiplied by the
+          // d-component scales s_a s_b s_c s_d that every contraction needs
+          const double sab = comp_scale_rt(C::LA, ab / NB) * comp_scale_rt(C::LB, ab % NB);
 #pragma unroll
-        for (int cd = 0; cd < NCD; ++cd) I[ab * NCD + cd] = y[cd];
+          for (int cd = 0; cd < NCD; ++cd)
+            Id[ab * NCD + cd] = (double)y[cd] * (sab * comp_scale_rt(C::LC, cd / ND) * comp_scale_rt(C::LD, cd % ND));
+        } else {
+#pragma unroll
+          for (int cd = 0; cd < NCD; ++cd) I[ab * NCD + cd] = y[cd];
+        }
       }
     }
     __syncwarp();
@@ -670,50 +681,58 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
     if (bp == kp) wdeg *= 0.5;
     const int a0 = bra.bfA, b0 = bra.bfB, c0 = ket.bfA, d0 = ket.bfB;
     auto Dsc = [&](int r0, int lr, int i, int c0_, int lc, int j) {
-      return __ldg(D + (size_t)(r0 + i) * nbf + c0_ + j) * comp_scale_rt(lr, i) * comp_scale_rt(lc, j);
+      const double dv = __ldg(D + (size_t)(r0 + i) * nbf + c0_ + j);
+      if constexpr (kPre) return dv;
+      else return dv * comp_scale_rt(lr, i) * comp_scale_rt(lc, j);
     };
-    auto Iv = [&](int a, int b, int c, int d) { return (double)I[((a * NB + b) * NC + c) * ND + d]; };
+    auto Iv = [&](int a, int b, int c, int d) {
+      if constexpr (kPre) return Id[((a * NB + b) * NC + c) * ND + d];
+      else return (double)I[((a * NB + b) * NC + c) * ND + d];
+    };
+    // scale of an output element: in the pre-scaled forms all four
+    // component scales are already inside the integrals
+    auto osc = [&](int l1, int i, int l2, int j) { return kPre ? 1.0 : comp_scale_rt(l1, i) * comp_scale_rt(l2, j); };
     for (int o = lane; o < NAB; o += 32) {  // J'_ab = w sum_cd I D_cd
       const int a = o / NB, b = o % NB;
       double acc2 = 0.0;
       for (int c = 0; c < NC; ++c)
         for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsc(c0, C::LC, c, d0, C::LD, d), acc2);
-      atomicAdd(J + (size_t)(a0 + a) * nbf + b0 + b, acc2 * wdeg * comp_scale_rt(C::LA, a) * comp_scale_rt(C::LB, b));
+      atomicAdd(J + (size_t)(a0 + a) * nbf + b0 + b, acc2 * wdeg * osc(C::LA, a, C::LB, b));
     }
     for (int o = lane; o < NCD; o += 32) {  // J'_cd = w sum_ab I D_ab
       const int c = o / ND, d = o % ND;
       double acc2 = 0.0;
       for (int a = 0; a < C::NA; ++a)
         for (int b = 0; b < NB; ++b) acc2 = fma(Iv(a, b, c, d), Dsc(a0, C::LA, a, b0, C::LB, b), acc2);
-      atomicAdd(J + (size_t)(c0 + c) * nbf + d0 + d, acc2 * wdeg * comp_scale_rt(C::LC, c) * comp_scale_rt(C::LD, d));
+      atomicAdd(J + (size_t)(c0 + c) * nbf + d0 + d, acc2 * wdeg * osc(C::LC, c, C::LD, d));
     }
     for (int o = lane; o < C::NA * NC; o += 32) {  // K'_ac = w sum_bd I D_bd
       const int a = o / NC, c = o % NC;
       double acc2 = 0.0;
       for (int b = 0; b < NB; ++b)
         for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsc(b0, C::LB, b, d0, C::LD, d), acc2);
-      atomicAdd(Kx + (size_t)(a0 + a) * nbf + c0 + c, acc2 * wdeg * comp_scale_rt(C::LA, a) * comp_scale_rt(C::LC, c));
+      atomicAdd(Kx + (size_t)(a0 + a) * nbf + c0 + c, acc2 * wdeg * osc(C::LA, a, C::LC, c));
     }
     for (int o = lane; o < C::NA * ND; o += 32) {  // K'_ad = w sum_bc I D_bc
       const int a = o / ND, d = o % ND;
       double acc2 = 0.0;
       for (int b = 0; b < NB; ++b)
         for (int c = 0; c < NC; ++c) acc2 = fma(Iv(a, b, c, d), Dsc(b0, C::LB, b, c0, C::LC, c), acc2);
-      atomicAdd(Kx + (size_t)(a0 + a) * nbf + d0 + d, acc2 * wdeg * comp_scale_rt(C::LA, a) * comp_scale_rt(C::LD, d));
+      atomicAdd(Kx + (size_t)(a0 + a) * nbf + d0 + d, acc2 * wdeg * osc(C::LA, a, C::LD, d));
     }
     for (int o = lane; o < NB * NC; o += 32) {  // K'_bc = w sum_ad I D_ad
       const int b = o / NC, c = o % NC;
       double acc2 = 0.0;
       for (int a = 0; a < C::NA; ++a)
         for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsc(a0, C::LA, a, d0, C::LD, d), acc2);
-      atomicAdd(Kx + (size_t)(b0 + b) * nbf + c0 + c, acc2 * wdeg * comp_scale_rt(C::LB, b) * comp_scale_rt(C::LC, c));
+      atomicAdd(Kx + (size_t)(b0 + b) * nbf + c0 + c, acc2 * wdeg * osc(C::LB, b, C::LC, c));
     }
     for (int o = lane; o < NB * ND; o += 32) {  // K'_bd = w sum_ac I D_ac
       const int b = o / ND, d = o % ND;
       double acc2 = 0.0;
       for (int a = 0; a < C::NA; ++a)
         for (int c = 0; c < NC; ++c) acc2 = fma(Iv(a, b, c, d), Dsc(a0, C::LA, a, c0, C::LC, c), acc2);
-      atomicAdd(Kx + (size_t)(b0 + b) * nbf + d0 + d, acc2 * wdeg * comp_scale_rt(C::LB, b) * comp_scale_rt(C::LD, d));
+      atomicAdd(Kx + (size_t)(b0 + b) * nbf + d0 + d, acc2 * wdeg * osc(C::LB, b, C::LD, d));
     }
     __syncwarp();
   }
