@@ -43,10 +43,11 @@ struct Request {
 
 int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 
-// Device bytes an admitted request holds: primitive-pair records (80 + 48
-// B), shell-pair info and ket lists, work lists (bounded by the bucket
-// count per pair), Boys-free SCF state: 12 n^2 matrices + DIIS 2 m n^2 +
-// syevd workspace, plus 10%.
+// Device bytes an admitted request holds: primitive-pair records (FP64 80 B,
+// FP32 48 B and df64 80 B per primitive pair), shell-pair info and ket
+// lists, work lists (bounded by the bucket count per pair), SCF state: 12
+// n^2 matrices plus two for the syevd workspace and host-pointer staging,
+// DIIS 2 m n^2, plus 10%.
 size_t estimate_footprint(const hf_request* r, int diis) {
   long long nbf = 0, npp = 0, np = 0;
   for (int s = 0; s < r->nshell; ++s) nbf += ncart(r->shells[s].l);
@@ -56,7 +57,7 @@ size_t estimate_footprint(const hf_request* r, int diis) {
       ++np;
     }
   const double n2 = (double)nbf * nbf * 8.0;
-  double bytes = npp * 128.0 + np * 64.0 + np * 2.0 * 16.0 * 4.0 * 6.0 + (14.0 + 2.0 * diis) * n2;
+  double bytes = npp * 208.0 + np * 64.0 + np * 2.0 * 16.0 * 4.0 * 6.0 + (14.0 + 2.0 * diis) * n2;
   return (size_t)(1.1 * bytes) + (1u << 20);
 }
 
