@@ -570,8 +570,10 @@ def run_batch(args):
                 "batch_conv": bool(r.converged), "batch_it": int(r.iterations), "gap": float(p.homo_lumo_gap),
                 "dE": float(abs(r.energy - p.energy))}
                for m, b, p, r in zip(mols, bases, plain, res_last)]
-    line = {"metric": "molecule Fock builds/s", "unit": "builds/s", "value": out["batch_mixed_df64"]["mol_fock_builds_per_s"],
-            "dtype": "f64+f32", "data": "synthetic",
+    # headline: the df64 batch, the fastest form that keeps |dE| <= 1e-8 against
+    # the FP64 solves (the FP32 split does not on molecules of ~50 atoms)
+    line = {"metric": "molecule Fock builds/s", "unit": "builds/s", "value": out["batch_df64"]["mol_fock_builds_per_s"],
+            "dtype": "df64", "data": "synthetic",
             "config": {"workload": f"first {len(mols)} of 512 molecules, atoms U[4,60], s+p, seeds 1000+i",
                        "e_tol": args.e_tol,
                        "nbf_total": int(sum(b.nbf for b in bases))},
