@@ -77,3 +77,30 @@ def test_generated_header_is_current():
         subprocess.run([sys.executable, gen, out, "2"], check=True)
         assert open(out).read() == open(os.path.join(ROOT, "paper_1303_4916_gb300", "csrc",
                                                       "eri_classes.cuh")).read()
+
+
+def test_binding_constants_match_header():
+    """Every integer #define of the header (status codes, flags, sizes) has
+    the same value in the binding."""
+    from paper_1303_4916_gb300 import _abi
+    defs = {}
+    for h in HEADERS:
+        for m in re.finditer(r"^#define\s+(HF_\w+)\s+\(?(-?\d+)u?\)?", open(h).read(), flags=re.M):
+            defs[m.group(1)] = int(m.group(2))
+    assert len(defs) > 15
+    for name, v in defs.items():
+        if hasattr(_abi, name):
+            assert getattr(_abi, name) == v, name
+    for name in ("HF_OK", "HF_PENDING", "HF_ERR_INVALID", "HF_ERR_TOO_LARGE", "HF_JK_DF64", "HF_JK_HOST",
+                 "HF_JK_FP32_BOYS", "HF_NCLASS"):
+        assert hasattr(_abi, name) and name in defs, name
+
+
+def test_jk_opts_sets_the_header_flags(lib):
+    import paper_1303_4916_gb300 as hf
+    from paper_1303_4916_gb300 import _abi
+    d = hf.jk_opts()
+    assert d.schwarz_tau == 1e-12 and d.fp32_bound == 0.0 and d.flags == 0
+    o = hf.jk_opts(schwarz_tau=0.0, fp32_bound=1e-5, host=True, fp32_boys=True, df64=True)
+    assert o.schwarz_tau == 0.0 and o.fp32_bound == 1e-5
+    assert o.flags == _abi.HF_JK_HOST | _abi.HF_JK_FP32_BOYS | _abi.HF_JK_DF64
