@@ -48,7 +48,8 @@ static const double OR_PI = 3.14159265358979323846264338327950288;
 /* Boys function                                                        */
 /* ------------------------------------------------------------------ */
 
-/* F_m(T) for one m.  T < 30: e^{-T} sum_i (2T)^i / prod_{k=0..i} (2m+2k+1),
+/* F_m(T) for one m: the Boys function through which the Gaussian integrals
+ * of Eqs. 4-5 are expressed.  T < 30: e^{-T} sum_i (2T)^i / prod_{k=0..i} (2m+2k+1),
  * summed in long double until the term is below 1e-22 of the sum.
  * T >= 30: F_0 = (1/2) sqrt(pi/T) erf(sqrt T), then upward recursion
  * F_{k+1} = ((2k+1) F_k - e^{-T}) / (2T). */
@@ -107,7 +108,7 @@ static void cart_powers(int l, int idx, int *lx, int *ly, int *lz)
         }
 }
 
-/* Primitive normalisation of x^a y^b z^c exp(-alpha r^2). */
+/* Primitive normalisation of x^a y^b z^c exp(-alpha r^2) (the Gaussians of Eq. 1). */
 static double prim_norm(double alpha, int a, int b, int c)
 {
     int L = a + b + c;
@@ -131,7 +132,9 @@ void or_basis_free(or_basis *B)
     free(B->bf_coef); free(B->bf_coef_off); free(B);
 }
 
-/* Returns NULL on invalid input (l > OR_LMAX, nprim < 1, bad index). */
+/* Contracted basis of Eq. 1: each Cartesian component sum_k d_k N_k g_k,
+ * rescaled to unit self-overlap.  Returns NULL on invalid input (l > OR_LMAX,
+ * nprim < 1, bad index). */
 or_basis *or_basis_new(int natom, const int *Z, const double *xyz, int nshell,
                        const int *sh_atom, const int *sh_l, const int *sh_nprim,
                        const int *sh_prim, int nprim_total, const double *exps,
@@ -222,7 +225,7 @@ static double binom(int n, int k)
     return r;
 }
 
-/* 1D overlap factor of (x-A)^la (x-B)^lb exp(-p (x-P)^2) by binomial
+/* Overlap integrals, Eq. 2.  1D factor of (x-A)^la (x-B)^lb exp(-p (x-P)^2) by binomial
  * expansion about P: sum_ij C(la,i) C(lb,j) PA^{la-i} PB^{lb-j}
  * int u^{i+j} e^{-p u^2} du. */
 static double tho_overlap_1d(int la, int lb, double PA, double PB, double p)
@@ -251,7 +254,7 @@ static double prim_overlap(double a, const double *A, const int *la, double b,
     return exp(-mu * r2) * s;
 }
 
-/* Kinetic energy of two primitives: the ket is differentiated,
+/* Kinetic energy integrals, Eq. 3, of two primitives: the ket is differentiated,
  * -1/2 <a|nabla^2|b> = b(2(lx+ly+lz)+3) <a|b> - 2 b^2 sum_x <a|b+2_x>
  *                      - 1/2 sum_x lx(lx-1) <a|b-2_x>. */
 static double prim_kinetic(double a, const double *A, const int *la, double b,
@@ -344,7 +347,7 @@ static void hermite_R(or_ws *ws, int L, double alpha, double X, double Y, double
                 Rout[(t * RD + u) * RD + v] = work[0][t][u][v];
 }
 
-/* Nuclear attraction of two primitives to a unit charge at C:
+/* Nuclear attraction integrals, Eq. 4, of two primitives to a unit charge at C:
  * <a| 1/|r-C| |b> = (2 pi / p) K_ab sum_tuv E^x_t E^y_u E^z_v R_tuv(p, P-C). */
 static double prim_nuclear(or_ws *ws, double a, const double *A, const int *la, double b,
                            const double *B, const int *lb, const double *C)
@@ -397,7 +400,8 @@ void or_one_electron(const or_basis *B, double *S, double *T, double *V)
     free(ws);
 }
 
-/* Nuclear repulsion sum_{A<B} Z_A Z_B / R_AB. */
+/* Nuclear repulsion sum_{A<B} Z_A Z_B / R_AB, the constant term of the total
+ * energy (Szabo-Ostlund, the textbook the paper's SCF follows). */
 double or_nuclear_repulsion(const or_basis *B)
 {
     double e = 0.0;
@@ -533,7 +537,8 @@ void or_eri_shell_block(const or_basis *B, int sA, int sB, int sC, int sD, doubl
     free(ws);
 }
 
-/* Q_AB = sqrt(max_{a in A, b in B} |(ab|ab)|) for all shell pairs,
+/* Schwarz factors (not in the paper: the screening rule is a reading of it).
+ * Q_AB = sqrt(max_{a in A, b in B} |(ab|ab)|) for all shell pairs,
  * nshell x nshell row-major (symmetric); the shell loop is split over the
  * OpenMP threads (each writes its own entries). */
 void or_schwarz(const or_basis *B, double *Q)
@@ -563,7 +568,7 @@ void or_schwarz(const or_basis *B, double *Q)
     }
 }
 
-/* All N^4 integrals (small N only), row-major [i][j][k][l]. */
+/* All N^4 integrals of Eq. 5 (small N only), row-major [i][j][k][l]. */
 void or_eri_tensor(const or_basis *B, double *G)
 {
     int n = B->nbf, ns = B->nshell;
@@ -625,8 +630,9 @@ static int unique_in_block(int A, int B, int C, int D, int i, int j, int k, int 
     return 0;
 }
 
-/* J and K for a density P (nbf x nbf, row-major), over the unique shell
- * quartets A>=B, C>=D, (AB)>=(CD), each integral then expanded through
+/* J and K of the J/K equation (Sec. "Technical details") for a density P
+ * (nbf x nbf, row-major), over the unique shell quartets A>=B, C>=D,
+ * (AB)>=(CD), each integral then expanded through
  * digest().  tau > 0 enables the Schwarz rule with the oracle's own Q.
  * nthreads > 1 splits the outer shell loop over OpenMP threads, each with
  * private J, K that are summed at the end.  Returns the number of shell

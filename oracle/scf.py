@@ -59,6 +59,8 @@ class RHFResult:
 
 
 def lowdin(S: np.ndarray, min_eig: float = 1e-10) -> np.ndarray:
+    """Symmetric (Loewdin) orthogonaliser X = S^(-1/2) = U s^(-1/2) U^T, step 1
+    of the Szabo-Ostlund procedure; LinearDependence below min_eig."""
     s, U = np.linalg.eigh(S)
     if s[0] < min_eig:
         raise LinearDependence(f"lambda_min(S) = {s[0]:.3e} < {min_eig:g}")
@@ -66,7 +68,8 @@ def lowdin(S: np.ndarray, min_eig: float = 1e-10) -> np.ndarray:
 
 
 def diis_extrapolate(Fs, es):
-    """Pulay DIIS: returns sum_i c_i F_i with sum_i c_i = 1 minimising |sum c_i e_i|."""
+    """Pulay DIIS (named in Sec. "Technical details"): returns sum_i c_i F_i
+    with sum_i c_i = 1 minimising |sum c_i e_i|."""
     Fs = list(Fs)
     es = list(es)
     while len(Fs) >= 2:
@@ -92,6 +95,9 @@ def diis_extrapolate(Fs, es):
 def rhf(mol, max_iter: int = 30, e_tol: float = 1e-8, diis_size: int = 0,
         tau: float = 0.0, nthreads: int = 1, basis: Optional[Basis] = None,
         D0: Optional[np.ndarray] = None) -> RHFResult:
+    """Closed-shell RHF by the steps of the module docstring (Szabo-Ostlund,
+    the procedure the paper's Hartree-Fock follows; J/K from the oracle's
+    integrals, optionally Schwarz-screened with its own factors)."""
     B = basis if basis is not None else Basis(mol)
     S, T, V = B.one_electron()
     H = T + V
