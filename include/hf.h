@@ -57,7 +57,8 @@ extern "C" {
 #define HF_ERR_NOT_FOUND (-9)      /* unknown serving ticket */
 #define HF_ERR_QUEUE_FULL (-10)    /* serving queue at capacity */
 #define HF_ERR_CANCELLED (-11)     /* request cancelled / server shut down */
-#define HF_ERR_TOO_LARGE (-12)     /* request footprint exceeds the HBM budget */
+#define HF_ERR_TOO_LARGE (-12)     /* request footprint exceeds the HBM budget, or a
+                                      class's work list exceeds 2^30 items */
 
 #define HF_LMAX 2                  /* highest shell angular momentum (d) */
 
@@ -185,7 +186,8 @@ int hf_count_quartets(hf_basis* b, const hf_jk_opts* opts, long long* n_total, l
  * symmetric density P = D:  J_ij = sum_kl (ij|kl) D_kl,
  * K_il = sum_jk (ij|kl) D_jk.  D, J, K are nbf x nbf, device pointers
  * (host pointers with HF_JK_HOST).  J and K are overwritten.  opts may be
- * NULL (defaults).  Errors: HF_ERR_INVALID, HF_ERR_CUDA, HF_ERR_OOM. */
+ * NULL (defaults).  Errors: HF_ERR_INVALID, HF_ERR_CUDA, HF_ERR_OOM,
+ * HF_ERR_TOO_LARGE (an angular class with more than 2^30 work items). */
 int hf_fock_jk(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts* opts);
 
 /* Work statistics of one canonical class (la lb | lc ld), for roofline

@@ -423,10 +423,14 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
           for (int r = 0; r < 2; ++r) {
             const int cnt = hi_[r] - lo_[r];
             if (cnt <= 0) continue;
+            // item offsets are int on the device: stop before the running
+            // sum could pass the limit (checked in 64 bits, per entry)
+            const long long next = (long long)io[r].back() + (cnt + chunk - 1) / chunk;
+            if (next > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "class %d: too many work items", cls);
             bra[r].push_back(pi);
             kb[r].push_back(lo_[r]);
             ke[r].push_back(hi_[r]);
-            io[r].push_back(io[r].back() + (cnt + chunk - 1) / chunk);
+            io[r].push_back((int)next);
             nq[r] += cnt;
           }
         }
@@ -434,7 +438,6 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
       for (int r = 0; r < 2; ++r) {
         ClassWork& w = r == 0 ? b->work64[cls] : b->work32[cls];
         const int nb = (int)bra[r].size();
-        if (io[r].back() > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "class %d: too many work items", cls);
         HF_CHECK(w.bra.alloc(ctx, nb));
         HF_CHECK(w.kbeg.alloc(ctx, nb));
         HF_CHECK(w.kend.alloc(ctx, nb));

@@ -69,16 +69,18 @@ int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vec
       const ClassWork& cw = r == 0 ? mols[m]->work64[cls] : mols[m]->work32[cls];
       for (size_t e = 0; e < cw.bra_h.size(); ++e) {
         const int cnt = cw.kend_h[e] - cw.kbeg_h[e];
+        // item offsets are int on the device: checked in 64 bits per entry
+        const long long next = (long long)hio.back() + (cnt + ctx->ops[cls].chunk - 1) / ctx->ops[cls].chunk;
+        if (next > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "batched class %d: too many work items", cls);
         hb.push_back(cw.bra_h[e]);
         hkb.push_back(cw.kbeg_h[e]);
         hke.push_back(cw.kend_h[e]);
         hm.push_back(m);
-        hio.push_back(hio.back() + (cnt + ctx->ops[cls].chunk - 1) / ctx->ops[cls].chunk);
+        hio.push_back((int)next);
         nq += cnt;
         mol_quartets[m] += cnt;
       }
     }
-    if (hio.back() > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "batched class %d: too many work items", cls);
     const int nb = (int)hb.size();
     HF_CHECK(bra[c2].alloc(ctx, nb));
     HF_CHECK(kbeg[c2].alloc(ctx, nb));
