@@ -61,6 +61,7 @@ extern "C" {
                                       class's work list exceeds 2^30 items */
 
 #define HF_LMAX 2                  /* highest shell angular momentum (d) */
+#define HF_MAX_NPRIM 16            /* most primitives in one contracted shell */
 
 /* ---------------------------------------------------------------- types */
 
@@ -160,8 +161,10 @@ void hf_ctx_inject_alloc_failure(hf_ctx* ctx, int n);
  * prefactors per primitive pair), Schwarz factors Q_ab and the
  * class-bucketed quartet work lists.  All input arrays are host memory and
  * are copied.  n_electrons must be even (closed shell).
- * Errors: HF_ERR_INVALID, HF_ERR_UNSUPPORTED_L (l > HF_LMAX),
- * HF_ERR_ODD_ELECTRONS, HF_ERR_OOM, HF_ERR_CUDA. */
+ * Errors: HF_ERR_INVALID (also a shell with more than HF_MAX_NPRIM
+ * primitives, a contraction of zero norm, two charged atoms at one point),
+ * HF_ERR_UNSUPPORTED_L (l > HF_LMAX), HF_ERR_ODD_ELECTRONS, HF_ERR_OOM,
+ * HF_ERR_CUDA. */
 int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, const hf_shell* shells,
                     int nshell, const double* exps, const double* coefs, int n_electrons,
                     hf_basis** out);

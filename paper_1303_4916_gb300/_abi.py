@@ -26,6 +26,7 @@ HF_ERR_QUEUE_FULL = -10
 HF_ERR_CANCELLED = -11
 HF_ERR_TOO_LARGE = -12
 HF_LMAX = 2
+HF_MAX_NPRIM = 16
 
 HF_JK_HOST = 1
 HF_JK_DETERMINISTIC = 2

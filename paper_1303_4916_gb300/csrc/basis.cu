@@ -10,7 +10,6 @@
 #include "eri.cuh"
 #include "hf_internal.h"
 
-#define HF_MAX_NPRIM 16
 static const double kPi = 3.14159265358979323846;
 
 // Primitive pairs whose magnitude bound is below this are skipped; their
