@@ -5,8 +5,8 @@ CPU-baseline leg of ``bench.py`` may import this package; the library under
 ``paper_1303_4916_gb300/`` never does, and this package never imports it.
 
 ``Basis`` wraps the plain C implementation in ``hf_oracle.c`` (integrals,
-Boys function, J/K); ``rhf`` in ``scf.py`` runs the textbook RHF iteration
-on top of it with numpy.
+Boys function, J/K); ``rhf`` and ``uhf`` in ``scf.py`` run the textbook RHF
+and unrestricted (Pople-Nesbet) iterations on top of it with numpy.
 """
 from .core import Basis, boys, build_oracle, oracle_threads  # noqa: F401
-from .scf import rhf, RHFResult, LinearDependence  # noqa: F401
+from .scf import rhf, uhf, RHFResult, UHFResult, LinearDependence  # noqa: F401

@@ -145,3 +145,79 @@ def rhf(mol, max_iter: int = 30, e_tol: float = 1e-8, diis_size: int = 0,
     return RHFResult(energy=E, e_elec=E - e_nuc, e_nuc=e_nuc, converged=converged,
                      iterations=k, D=D, C=C, eps=eps, F=Fk, F1=F1, energies=energies,
                      homo_lumo_gap=gap, diis_error=float(np.abs(err).max()), H=H, S=S)
+
+
+@dataclass
+class UHFResult:
+    energy: float
+    e_nuc: float
+    converged: bool
+    iterations: int
+    Da: np.ndarray
+    Db: np.ndarray
+    Ca: np.ndarray
+    Cb: np.ndarray
+    eps_a: np.ndarray
+    eps_b: np.ndarray
+    s2: float               # <S^2> of the UHF determinant
+    energies: List[float] = field(default_factory=list)
+
+
+def uhf(mol, n_alpha: int, n_beta: int, max_iter: int = 128, e_tol: float = 1e-8, diis_size: int = 0,
+        tau: float = 0.0, nthreads: int = 1, basis: Optional[Basis] = None) -> UHFResult:
+    """Unrestricted HF (the paper's test calculations are UHF), by the
+    Pople-Nesbet equations as Szabo-Ostlund state them:
+
+      D^s = C^s_occ C^s_occ^T (s = alpha, beta; n_alpha and n_beta columns),
+      F^s = H + J[D^a + D^b] - K[D^s]   (J, K of the J/K equation, no factors),
+      E = (1/2) sum_s Tr[D^s (H + F^s)] + E_nuc,
+
+    X = S^(-1/2), core guess F^a = F^b = H, stop at |E_k - E_{k-1}| <= e_tol.
+    With DIIS the alpha and beta errors e^s = F^s D^s S - S D^s F^s form one
+    vector and share one set of coefficients.  <S^2> = S_z (S_z + 1) + n_beta
+    - sum_ij |(C^a_occ^T S C^b_occ)_ij|^2 with S_z = (n_alpha - n_beta) / 2."""
+    B = basis if basis is not None else Basis(mol)
+    S, T, V = B.one_electron()
+    H = T + V
+    e_nuc = B.nuclear_repulsion()
+    X = lowdin(S)
+    nocc = (n_alpha, n_beta)
+    F = [H.copy(), H.copy()]
+    e_old = None
+    energies = []
+    Fs, es = [], []
+    converged = False
+    k = 0
+    for k in range(1, max_iter + 1):
+        Cs, epss, Ds = [], [], []
+        for s in range(2):
+            eps, Cp = np.linalg.eigh(X.T @ F[s] @ X)
+            C = X @ Cp
+            Cs.append(C)
+            epss.append(eps)
+            Ds.append(C[:, :nocc[s]] @ C[:, :nocc[s]].T)
+        Ja, Ka, _ = B.jk(Ds[0], tau, nthreads)
+        Jb, Kb, _ = B.jk(Ds[1], tau, nthreads)
+        J = Ja + Jb                        # J is linear in D
+        Fk = [H + J - Ka, H + J - Kb]
+        E = 0.5 * sum(float(np.sum(Ds[s] * (H + Fk[s]))) for s in range(2)) + e_nuc
+        energies.append(E)
+        F = Fk
+        if diis_size > 0:
+            Fs.append(np.stack(Fk))
+            es.append(np.stack([Fk[s] @ Ds[s] @ S - S @ Ds[s] @ Fk[s] for s in range(2)]))
+            if len(Fs) > diis_size:
+                Fs.pop(0)
+                es.pop(0)
+            if len(Fs) >= 2:
+                Fx = diis_extrapolate(Fs, es)
+                F = [Fx[0], Fx[1]]
+        if e_old is not None and abs(E - e_old) <= e_tol:
+            converged = True
+            break
+        e_old = E
+    sz = 0.5 * (n_alpha - n_beta)
+    ov = Cs[0][:, :n_alpha].T @ S @ Cs[1][:, :n_beta]
+    s2 = sz * (sz + 1.0) + n_beta - float(np.sum(ov * ov))
+    return UHFResult(energy=E, e_nuc=e_nuc, converged=converged, iterations=k, Da=Ds[0], Db=Ds[1],
+                     Ca=Cs[0], Cb=Cs[1], eps_a=epss[0], eps_b=epss[1], s2=s2, energies=energies)

@@ -14,6 +14,8 @@
   the full tensor (a different code path in the oracle).
 * DIIS: the exact root of an affine error map, a null-space least-squares
   solve of the same constrained minimum; Loewdin: X S X = I.
+* UHF: one-electron closed form and core eigenvalue, UHF = RHF for closed
+  shells, spin-swap symmetry and the <S^2> >= S_z(S_z+1) bound.
 * The stored rows of the 150-atom molecule: made for the current input and
   symmetric where two stored rows cross.
 """
@@ -398,3 +400,55 @@ def test_lowdin_is_the_symmetric_inverse_square_root():
     assert np.abs(X @ X - np.linalg.inv(S)).max() < 1e-8 * np.abs(np.linalg.inv(S)).max()
     with pytest.raises(LinearDependence):
         lowdin(np.array([[1.0, 1.0], [1.0, 1.0 + 1e-13]]))
+
+
+# ---------------------------------------------------------------- UHF
+@pytest.mark.parametrize("alpha", [0.28, 1.0, 3.7])
+def test_uhf_one_electron_single_gaussian(alpha):
+    """One electron (H atom, one s Gaussian): the UHF two-electron terms
+    J[D^a] - K[D^a] cancel exactly, so E = <T> + <V> =
+    3 alpha / 2 - 2 sqrt(2 alpha / pi), and <S^2> = 3/4."""
+    m = _pack([1], [[0.2, 0.1, -0.4]], [(0, 0, [alpha], [1.0])], "h", 0, n_electrons=0)
+    r = oracle.uhf(m, 1, 0, max_iter=5, e_tol=1e-14)
+    assert r.energy == pytest.approx(1.5 * alpha - 2 * math.sqrt(2 * alpha / math.pi), rel=1e-13)
+    assert r.s2 == pytest.approx(0.75, abs=1e-14)
+
+
+def test_uhf_one_electron_is_the_lowest_core_eigenvalue():
+    """One electron in an s+p+d basis on three nuclei: no electron-electron
+    energy survives, so the UHF energy is the lowest root of the generalised
+    eigenproblem H c = e S c plus E_nuc (scipy's LAPACK, a different route)."""
+    from scipy.linalg import eigh
+    mol = lattice_molecule(3, 3, "spd")
+    B = oracle.Basis(mol)
+    S, T, V = B.one_electron()
+    e0 = eigh(T + V, S, eigvals_only=True)[0]
+    r = oracle.uhf(mol, 1, 0, max_iter=10, e_tol=1e-13)
+    assert r.energy == pytest.approx(e0 + B.nuclear_repulsion(), abs=1e-10)
+
+
+@pytest.mark.parametrize("diis", [0, 6])
+def test_uhf_closed_shell_equals_rhf(diis):
+    """n_alpha = n_beta from the same core guess keeps C^a = C^b, so UHF is
+    RHF: same energy (the RHF oracle is pinned above), <S^2> = 0."""
+    mol = h_line()
+    ro = oracle.rhf(mol, max_iter=80, e_tol=1e-11, diis_size=diis)
+    ru = oracle.uhf(mol, 4, 4, max_iter=80, e_tol=1e-11, diis_size=diis)
+    assert ru.converged and ru.energy == pytest.approx(ro.energy, abs=1e-9)
+    assert abs(ru.s2) < 1e-10
+    assert np.abs(ru.Da - ro.D).max() < 1e-6 and np.abs(ru.Db - ro.D).max() < 1e-6
+
+
+@pytest.mark.parametrize("natom,na,nb", [(5, 3, 2), (6, 4, 2)])
+def test_uhf_spin_swap_and_contamination_bound(natom, na, nb):
+    """Open shells on an H chain: swapping the alpha and beta counts changes
+    neither the energy nor <S^2>, and <S^2> is at least S_z (S_z + 1) (spin
+    contamination can only add)."""
+    mol = h_line(natom, seed=3)
+    r1 = oracle.uhf(mol, na, nb, max_iter=200, e_tol=1e-11, diis_size=6)
+    r2 = oracle.uhf(mol, nb, na, max_iter=200, e_tol=1e-11, diis_size=6)
+    assert r1.converged and r2.converged
+    assert r1.energy == pytest.approx(r2.energy, abs=1e-9)
+    assert r1.s2 == pytest.approx(r2.s2, abs=1e-7)
+    sz = 0.5 * (na - nb)
+    assert r1.s2 >= sz * (sz + 1) - 1e-10
