@@ -221,3 +221,25 @@ def uhf(mol, n_alpha: int, n_beta: int, max_iter: int = 128, e_tol: float = 1e-8
     s2 = sz * (sz + 1.0) + n_beta - float(np.sum(ov * ov))
     return UHFResult(energy=E, e_nuc=e_nuc, converged=converged, iterations=k, Da=Ds[0], Db=Ds[1],
                      Ca=Cs[0], Cb=Cs[1], eps_a=epss[0], eps_b=epss[1], s2=s2, energies=energies)
+
+
+def mp2(result: RHFResult, basis: Basis, n_occ: int) -> float:
+    """Second-order Moller-Plesset correlation energy of a converged
+    closed-shell RHF solution (the paper's MP2 follows Szabo-Ostlund):
+
+      E(2) = sum_{i,j occ} sum_{a,b virt} (ia|jb) [2 (ia|jb) - (ib|ja)]
+                                           / (e_i + e_j - e_a - e_b)
+
+    over the canonical spatial orbitals, (ia|jb) in chemists' notation from
+    the AO tensor by four one-index transformations (numpy contractions as
+    library steps).  Small bases only: it builds the N^4 AO tensor."""
+    G = basis.eri_tensor()
+    C, eps = result.C, result.eps
+    Co, Cv = C[:, :n_occ], C[:, n_occ:]
+    t = np.einsum("pqrs,pi->iqrs", G, Co)
+    t = np.einsum("iqrs,qa->iars", t, Cv)
+    t = np.einsum("iars,rj->iajs", t, Co)
+    iajb = np.einsum("iajs,sb->iajb", t, Cv)
+    eo, ev = eps[:n_occ], eps[n_occ:]
+    denom = eo[:, None, None, None] - ev[None, :, None, None] + eo[None, None, :, None] - ev[None, None, None, :]
+    return float(np.sum(iajb * (2.0 * iajb - iajb.transpose(0, 3, 2, 1)) / denom))

@@ -17,6 +17,8 @@
   solve of the same constrained minimum; Loewdin: X S X = I.
 * UHF: one-electron closed form and core eigenvalue, UHF = RHF for closed
   shells, spin-swap symmetry and the <S^2> >= S_z(S_z+1) bound.
+* MP2: minimal-basis H2 closed form, the spin-orbital antisymmetrised form,
+  size consistency with the R^-3 dipole tail.
 * The stored rows of the 150-atom molecule: made for the current input and
   symmetric where two stored rows cross.
 """
@@ -456,3 +458,75 @@ def test_uhf_spin_swap_and_contamination_bound(natom, na, nb):
     assert r1.s2 == pytest.approx(r2.s2, abs=1e-7)
     sz = 0.5 * (na - nb)
     assert r1.s2 >= sz * (sz + 1) - 1e-10
+
+
+# ---------------------------------------------------------------- MP2
+def _spin_orbital_mp2(r, B, n_occ):
+    """E(2) = 1/4 sum_{ijab} |<ij||ab>|^2 / (e_i + e_j - e_a - e_b) over spin
+    orbitals built from the spatial MOs (the antisymmetrised form), a
+    different formula from the oracle's spin-adapted one."""
+    G = B.eri_tensor()
+    C, eps = r.C, r.eps
+    n = C.shape[1]
+    mo = np.einsum("pqrs,pi,qj,rk,sl->ijkl", G, C, C, C, C, optimize=True)   # (ij|kl) over spatial MOs
+    ns = 2 * n
+    spat, spin = np.arange(ns) // 2, np.arange(ns) % 2
+    # <pq|rs> = (pr|qs) delta(spin p, spin r) delta(spin q, spin s)
+    same = (spin[:, None] == spin[None, :]).astype(float)
+    phys = mo[np.ix_(spat, spat, spat, spat)].transpose(0, 2, 1, 3) * same[:, None, :, None] * same[None, :, None, :]
+    anti = phys - phys.transpose(0, 1, 3, 2)
+    e = eps[spat]
+    occ, vir = np.arange(2 * n_occ), np.arange(2 * n_occ, ns)
+    A = anti[np.ix_(occ, occ, vir, vir)]
+    d = e[occ][:, None, None, None] + e[occ][None, :, None, None] - e[vir][None, None, :, None] - e[vir][None, None, None, :]
+    return 0.25 * float(np.sum(A * A / d))
+
+
+def test_mp2_minimal_basis_h2_closed_form():
+    """Minimal-basis H2: one occupied and one virtual orbital, so
+    E(2) = K12^2 / (2 (e1 - e2)) with K12 = (12|12) over the MOs."""
+    m, _ = _h2()
+    B = oracle.Basis(m)
+    r = oracle.rhf(m, max_iter=30, e_tol=1e-12)
+    G = B.eri_tensor()
+    c1, c2 = r.C[:, 0], r.C[:, 1]
+    K12 = np.einsum("pqrs,p,q,r,s->", G, c1, c2, c1, c2)
+    expect = K12 ** 2 / (2 * (r.eps[0] - r.eps[1]))
+    assert oracle.mp2(r, B, 1) == pytest.approx(expect, rel=1e-12)
+    assert expect < 0
+
+
+@pytest.mark.parametrize("mol_fn", [lambda: h_line(6, seed=4), lambda: lattice_molecule(3, 3, "sp")])
+def test_mp2_spin_adapted_equals_spin_orbital_form(mol_fn):
+    mol = mol_fn()
+    B = oracle.Basis(mol)
+    r = oracle.rhf(mol, max_iter=100, e_tol=1e-12, diis_size=6)
+    n_occ = mol.n_electrons // 2
+    assert oracle.mp2(r, B, n_occ) == pytest.approx(_spin_orbital_mp2(r, B, n_occ), rel=1e-10)
+
+
+def test_mp2_is_size_consistent():
+    """Two copies of a molecule far apart: the RHF and MP2 energies are
+    twice the single ones up to the dipole-dipole interaction, which falls
+    off as R^-3 (checked between 2000 and 10000 bohr).  With identical copies
+    the aufbau occupation of the pair is the two single occupations, and the
+    canonical MP2 sum is invariant to the mixing of degenerate pair orbitals."""
+    a = h_line(4, seed=8)
+    ra = oracle.rhf(a, max_iter=100, e_tol=1e-13, diis_size=6)
+    e2a = oracle.mp2(ra, oracle.Basis(a), a.n_electrons // 2)
+    assert e2a < 0
+    d = {}
+    for R in (2000.0, 10000.0):
+        shells = []
+        for k in range(2):
+            for s in range(a.nshell):
+                p0, n = a.shell_prim[s], a.shell_nprim[s]
+                shells.append((int(a.shell_atom[s]) + k * a.natom, int(a.shell_l[s]), a.exps[p0:p0 + n],
+                               a.coefs[p0:p0 + n]))
+        ab = _pack(np.concatenate([a.Z, a.Z]), np.vstack([a.xyz, a.xyz + np.array([0.0, R, 0.0])]), shells, "ab",
+                   0, n_electrons=2 * a.n_electrons)
+        r = oracle.rhf(ab, max_iter=100, e_tol=1e-13, diis_size=6)
+        d[R] = (r.energy - 2 * ra.energy, oracle.mp2(r, oracle.Basis(ab), a.n_electrons) - 2 * e2a)
+    assert abs(d[10000.0][0]) < 1e-10 and abs(d[10000.0][1]) < 1e-11
+    for k in range(2):
+        assert d[2000.0][k] / d[10000.0][k] == pytest.approx(125.0, rel=0.02)
