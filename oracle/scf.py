@@ -243,3 +243,33 @@ def mp2(result: RHFResult, basis: Basis, n_occ: int) -> float:
     eo, ev = eps[:n_occ], eps[n_occ:]
     denom = eo[:, None, None, None] - ev[None, :, None, None] + eo[None, None, :, None] - ev[None, None, None, :]
     return float(np.sum(iajb * (2.0 * iajb - iajb.transpose(0, 3, 2, 1)) / denom))
+
+
+def rhf_gradient(mol, h: float = 2e-3, e_tol: float = 1e-13, diis_size: int = 8, max_iter: int = 200) -> np.ndarray:
+    """Nuclear gradient dE/dR_A (natom x 3, Eh/bohr) of the converged RHF
+    energy; the force on atom A (the paper's HF forces) is its negative.
+
+    By its definition, the derivative of E with the basis functions moving
+    with their atoms: central differences at steps h and h/2 combined by
+    Richardson extrapolation, g = (4 g(h/2) - g(h)) / 3, error O(h^4).  Each
+    displaced SCF starts from the reference density so it converges to the
+    same state."""
+    ref = rhf(mol, max_iter=max_iter, e_tol=e_tol, diis_size=diis_size)
+    if not ref.converged:
+        raise RuntimeError("reference SCF did not converge")
+
+    def energy(a, x, d):
+        m = mol.copy()
+        m.xyz[a, x] += d
+        r = rhf(m, max_iter=max_iter, e_tol=e_tol, diis_size=diis_size, D0=ref.D)
+        if not r.converged:
+            raise RuntimeError("displaced SCF did not converge")
+        return r.energy
+
+    g = np.zeros((mol.natom, 3))
+    for a in range(mol.natom):
+        for x in range(3):
+            gh = (energy(a, x, h) - energy(a, x, -h)) / (2 * h)
+            gh2 = (energy(a, x, h / 2) - energy(a, x, -h / 2)) / h
+            g[a, x] = (4 * gh2 - gh) / 3
+    return g

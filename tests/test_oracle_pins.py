@@ -19,6 +19,8 @@
   shells, spin-swap symmetry and the <S^2> >= S_z(S_z+1) bound.
 * MP2: minimal-basis H2 closed form, the spin-orbital antisymmetrised form,
   size consistency with the R^-3 dipole tail.
+* Nuclear gradient: sympy's exact derivative of the closed-form H2 energy
+  (one s Gaussian per atom); zero net force and torque.
 * The stored rows of the 150-atom molecule: made for the current input and
   symmetric where two stored rows cross.
 """
@@ -530,3 +532,55 @@ def test_mp2_is_size_consistent():
     assert abs(d[10000.0][0]) < 1e-10 and abs(d[10000.0][1]) < 1e-11
     for k in range(2):
         assert d[2000.0][k] / d[10000.0][k] == pytest.approx(125.0, rel=0.02)
+
+
+# ---------------------------------------------------------------- forces
+def _h2_one_gaussian_energy():
+    """Closed-form RHF energy of H2 with one normalised s Gaussian (exponent
+    a) per atom at distance R: the bonding orbital is fixed by symmetry, and
+    every integral has a closed form in exp and F_0(t) = sqrt(pi/t) erf(sqrt t)/2,
+      E = 2 (h11 + h12) / (1 + S)
+          + [(11|11) + (11|22) + 2 (12|12) + 4 (11|12)] / (2 (1 + S)^2) + 1/R."""
+    sp = pytest.importorskip("sympy")
+    R, a = sp.symbols("R a", positive=True)
+    pi = sp.pi
+
+    def F0(t):
+        return sp.sqrt(pi / t) * sp.erf(sp.sqrt(t)) / 2
+    n2 = (2 * a / pi) ** sp.Rational(3, 2)                 # N^2, N = (2a/pi)^(3/4)
+    S = sp.exp(-a * R ** 2 / 2)
+    T11, T12 = 3 * a / 2, a / 2 * (3 - a * R ** 2) * S
+    v = -(2 * pi / (2 * a)) * n2                           # -(2 pi / p) N^2, p = 2a, unit charge
+    V11 = v + v * F0(2 * a * R ** 2)                       # nuclei on A and on B
+    V12 = 2 * v * S * F0(2 * a * (R / 2) ** 2)
+    g = 2 * pi ** sp.Rational(5, 2) / ((2 * a) ** 2 * sp.sqrt(4 * a)) * n2 ** 2
+    A, B = g, g * F0(a * R ** 2)
+    C, D = g * sp.exp(-a * R ** 2), g * S * F0(a * R ** 2 / 4)
+    E = 2 * (T11 + V11 + T12 + V12) / (1 + S) + (A + B + 2 * C + 4 * D) / (2 * (1 + S) ** 2) + 1 / R
+    return sp, R, a, E
+
+
+@pytest.mark.parametrize("alpha,dist", [(0.8, 1.4), (0.4, 2.2)])
+def test_rhf_gradient_matches_the_closed_form_derivative(alpha, dist):
+    """dE/dR of the closed form (sympy) against the oracle's gradient, which
+    differentiates its own SCF energy; the energies themselves first."""
+    sp, R, a, E = _h2_one_gaussian_energy()
+    m = _pack([1, 1], [[0, 0, 0], [dist, 0, 0]], [(0, 0, [alpha], [1.0]), (1, 0, [alpha], [1.0])], "h2", 0,
+              n_electrons=2)
+    e_ref = float(E.subs({R: dist, a: alpha}).evalf(30))
+    de_ref = float(sp.diff(E, R).subs({R: dist, a: alpha}).evalf(30))
+    assert oracle.rhf(m, max_iter=20, e_tol=1e-13).energy == pytest.approx(e_ref, abs=1e-12)
+    g = oracle.rhf_gradient(m)
+    assert g[1, 0] == pytest.approx(de_ref, abs=1e-8)
+    assert g[0, 0] == pytest.approx(-de_ref, abs=1e-8)
+    assert np.abs(g[:, 1:]).max() < 1e-8
+
+
+def test_rhf_gradient_is_translation_and_rotation_invariant():
+    """E does not change under rigid motions, so the gradients sum to zero
+    and exert no torque: sum_A g_A = 0, sum_A R_A x g_A = 0."""
+    mol = lattice_molecule(4, 5, "sp", charges=(1,), charge_p=(1.0,))   # four H, non-collinear
+    g = oracle.rhf_gradient(mol)
+    assert np.abs(g).max() > 1e-3
+    assert np.abs(g.sum(axis=0)).max() < 1e-7
+    assert np.abs(np.cross(mol.xyz, g).sum(axis=0)).max() < 1e-7
