@@ -36,7 +36,7 @@ extern "C" const char* hf_strerror(int code) {
     case HF_ERR_NOT_FOUND: return "not found";
     case HF_ERR_QUEUE_FULL: return "queue full";
     case HF_ERR_CANCELLED: return "cancelled";
-    case HF_ERR_TOO_LARGE: return "request exceeds memory budget";
+    case HF_ERR_TOO_LARGE: return "request exceeds the memory budget or a work-list limit";
     default: return "unknown error";
   }
 }

@@ -104,3 +104,25 @@ def test_jk_opts_sets_the_header_flags(lib):
     o = hf.jk_opts(schwarz_tau=0.0, fp32_bound=1e-5, host=True, fp32_boys=True, df64=True)
     assert o.schwarz_tau == 0.0 and o.fp32_bound == 1e-5
     assert o.flags == _abi.HF_JK_HOST | _abi.HF_JK_FP32_BOYS | _abi.HF_JK_DF64
+
+
+def test_header_is_plain_c99_and_a_c_program_links(lib, tmp_path):
+    """include/hf.h is a C interface: a C99 program (tests/c_abi_example.c)
+    compiles against it without warnings, links to libhf.so and runs; with
+    no GPU it stops at hf_ctx_create with HF_ERR_CUDA."""
+    import shutil
+    import subprocess
+    import torch
+    cc = shutil.which("gcc")
+    if not cc:
+        pytest.skip("no C compiler")
+    libdir = os.path.join(ROOT, "paper_1303_4916_gb300")
+    exe = str(tmp_path / "c_abi_example")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_abi_example.c"), "-L", libdir, "-lhf", f"-Wl,-rpath,{libdir}",
+                    "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert "tau 1e-12 max_iter 128" in out.stdout and "odd electron count" in out.stdout
+    if not torch.cuda.is_available():
+        assert "ctx -7" in out.stdout
