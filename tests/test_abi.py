@@ -126,3 +126,22 @@ def test_header_is_plain_c99_and_a_c_program_links(lib, tmp_path):
     assert "tau 1e-12 max_iter 128" in out.stdout and "odd electron count" in out.stdout
     if not torch.cuda.is_available():
         assert "ctx -7" in out.stdout
+
+
+def test_product_path_fails_loudly_without_the_library(tmp_path):
+    """With libhf.so absent the package raises ImportError on first use;
+    there is no CPU fallback to take over."""
+    import subprocess
+    import sys
+    code = (
+        "import paper_1303_4916_gb300._abi as a\n"
+        f"a.load.__defaults__ = ({str(tmp_path / 'libhf.so')!r},)\n"
+        "import paper_1303_4916_gb300 as hf\n"
+        "try:\n"
+        "    hf.jk_opts()\n"
+        "except ImportError as e:\n"
+        "    print('ImportError:', e)\n"
+        "else:\n"
+        "    print('no error')\n")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    assert "ImportError: libhf.so not built" in out.stdout, out.stdout + out.stderr
