@@ -220,16 +220,19 @@ int hf_fock_jk_profiled(hf_basis* b, const double* D, double* J, double* K, cons
  * has no counterpart: it is a deployment form of the J/K build above for
  * code where cudaMalloc is off limits when the Fock build runs (a frozen
  * allocator, a host framework that owns all device memory, a real-time
- * loop).  Same inputs, outputs and results as hf_fock_jk (device pointers
- * only); the J'/K' accumulators and work-item counters live in one static
+ * loop).  Same inputs, outputs, precision tiers (HF_JK_DF64,
+ * HF_JK_FP32_BOYS, fp32_bound) and results as hf_fock_jk, device pointers
+ * only; the J'/K' accumulators and work-item counters live in one static
  * device array of the library, so the call allocates nothing.
  * Limits: nbf <= 512 (HF_ERR_TOO_LARGE above); about 4 MiB of static device
  * memory is held on every GPU that loads the library until exit.
  * The first call on a device looks up the array's address (once per
- * device): make it before any stream capture.  All calls share the array,
- * so calls that overlap on the GPU race.  The quartet work lists for the
+ * device): make it before any stream capture, and do not use the entry
+ * point on a device after cudaDeviceReset.  All calls share the array, so
+ * calls that overlap on the GPU race.  The quartet work lists for the
  * options must already exist on the basis (a prior hf_fock_jk or
- * hf_count_quartets with the same options), else HF_ERR_INVALID. */
+ * hf_count_quartets with the same options), else HF_ERR_INVALID; a
+ * negative threshold is HF_ERR_INVALID as in hf_fock_jk. */
 int hf_fock_jk_noalloc(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts* opts);
 
 /* One-electron matrices of Eqs. 2-4 (device pointers, any may be NULL)

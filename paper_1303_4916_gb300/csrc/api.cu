@@ -125,27 +125,26 @@ int hf_boys_tables(hf_ctx* ctx) {
       }
     }
   }
-  // df64 table: grid T_i = i/16, per (order, row) 16 floats of F-coefficients
-  // (c_0..c_4 as hi/lo pairs, c_5..c_7 as floats) and 16 of exp coefficients
+  // df64 table: grid T_i = i/16, per (order, row) 16 floats: the Taylor
+  // coefficients of F_L (c_0..c_4 as hi/lo pairs, c_5..c_7 as floats), a pad,
+  // and exp(-T_i) as a hi/lo pair
   const size_t ndf = (size_t)(BOYS_LMAX + 1) * BOYSDF_NGRID * BOYSDF_ROW;
   std::vector<float> tdf(ndf, 0.0f);
+  auto split = [](long double c, float* q) {
+    const float h = (float)c;
+    q[0] = h;
+    q[1] = (float)(c - (long double)h);
+  };
   for (int i = 0; i < BOYSDF_NGRID; ++i) {
     boys_row((long double)i / 16.0L, F, &et);
     for (int L = 0; L <= BOYS_LMAX; ++L) {
       float* r = &tdf[((size_t)L * BOYSDF_NGRID + i) * BOYSDF_ROW];
-      for (int half = 0; half < 2; ++half) {
-        float* q = r + 16 * half;
-        for (int k = 0; k < 8; ++k) {
-          const long double c = (half == 0 ? F[L + k] : et) / fact[k];
-          if (k < 5) {
-            const float h = (float)c;
-            q[2 * k] = h;
-            q[2 * k + 1] = (float)(c - (long double)h);
-          } else {
-            q[10 + (k - 5)] = (float)c;
-          }
-        }
+      for (int k = 0; k < 8; ++k) {
+        const long double c = F[L + k] / fact[k];
+        if (k < 5) split(c, r + 2 * k);
+        else r[10 + (k - 5)] = (float)c;
       }
+      split(et, r + 14);
     }
   }
   void* p = nullptr;

@@ -101,23 +101,28 @@ __global__ void pair_kernel(int npairs, const int* __restrict__ pA, const int* _
 }
 
 // ------------------------------------------------------------- symmetrise
-// J = 2 (J' + J'^T), K = K' + K'^T in place.
-__global__ void symmetrize_jk(double* __restrict__ J, double* __restrict__ K, int n) {
+// J = 2 (J' + J'^T), K = K' + K'^T (and K2 = K2' + K2'^T when K2 is given),
+// from the accumulators into (J, K, K2).  In place when the accumulators
+// are the outputs: each unordered pair {i, j} is read and written by one
+// thread only, so the two forms share this kernel.
+__global__ void symmetrize_jk(const double* Jp, const double* Kp, double* J, double* K, const double* K2p, double* K2,
+                              int n) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long tot = (long long)n * n;
   if (t >= tot) return;
   const int i = (int)(t / n), j = (int)(t % n);
   if (j < i) return;
   const size_t ij = (size_t)i * n + j, ji = (size_t)j * n + i;
-  if (J) {
-    const double s = 2.0 * (J[ij] + J[ji]);
-    J[ij] = s;
-    J[ji] = s;
-  }
-  if (K) {
-    const double s = K[ij] + K[ji];
-    K[ij] = s;
-    K[ji] = s;
+  const double sj = 2.0 * (Jp[ij] + Jp[ji]);
+  const double sk = Kp[ij] + Kp[ji];
+  J[ij] = sj;
+  J[ji] = sj;
+  K[ij] = sk;
+  K[ji] = sk;
+  if (K2) {
+    const double s2 = K2p[ij] + K2p[ji];
+    K2[ij] = s2;
+    K2[ji] = s2;
   }
 }
 
@@ -489,11 +494,56 @@ extern "C" int hf_count_quartets(hf_basis* b, const hf_jk_opts* opts, long long*
   return HF_OK;
 }
 
-static int launch_grid(hf_ctx* ctx, int occ, int nitems) {
+int hf_launch_grid(hf_ctx* ctx, int occ, int nitems) {
   const int warps = 4;
   int g = (nitems + warps - 1) / warps;
   const int cap = std::max(1, occ) * ctx->num_sms;
   return std::max(1, std::min(g, cap));
+}
+
+LaunchShape hf_launch_shape(const hf_ctx* ctx, int occ, int nitems, int cap_per_sm) {
+  const int per_sm = std::max(1, cap_per_sm > 0 ? std::min(occ, cap_per_sm) : occ);
+  const long long slots = 4LL * per_sm * ctx->num_sms;  // resident warps
+  if (nitems >= slots) return LaunchShape{std::max(1, per_sm * ctx->num_sms), 128};
+  return LaunchShape{std::max(1, nitems), 32};
+}
+
+int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, double* K, int* counters,
+              const hf_jk_opts& o, cudaStream_t st, long long* nq, JKClassTiming* timing) {
+  hf_ctx* ctx = b->ctx;
+  const PairSet ps = hf_pairset(b);
+  const KernelCommon kc = hf_kernel_common(ctx, o.flags);
+  const MolJK one{D, Jp, Kp, b->nbf, 0};
+  long long total = 0;
+  if (timing) {
+    timing->n = 0;
+    HF_CUDA(cudaEventRecord(timing->ev[timing->n++], st));
+  }
+  // heaviest classes first
+  for (int c = HF_NCLASS - 1; c >= 0; --c) {
+    const EriClassOps& op = ctx->ops[c];
+    for (int r = 0; r < 2; ++r) {
+      const ClassWork& cw = r == 0 ? b->work64[c] : b->work32[c];
+      total += cw.nquartets;
+      if (cw.w.nitems <= 0) continue;
+      JKWork w = cw.w;
+      w.counter = counters + 2 * c + r;
+      const jk_launch_fn fn = r == 0 ? hf_jk_hi(op, o.flags) : op.jk32;
+      const int occ = r == 0 ? hf_occ_hi(op, o.flags) : op.occ32();
+      const LaunchShape sh = hf_launch_shape(ctx, occ, w.nitems);
+      fn(w, ps, kc, one, nullptr, sh.grid, sh.threads, st);
+      if (timing) {
+        timing->which[timing->n - 1] = 2 * c + r;
+        HF_CUDA(cudaEventRecord(timing->ev[timing->n++], st));
+      }
+    }
+  }
+  HF_CUDA(cudaGetLastError());
+  const size_t nn = (size_t)b->nbf * b->nbf;
+  symmetrize_jk<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Jp, Kp, J, K, nullptr, nullptr, b->nbf);
+  HF_CUDA(cudaGetLastError());
+  if (nq) *nq = total;
+  return HF_OK;
 }
 
 int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts& o, long long* nq) {
@@ -504,25 +554,7 @@ int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const 
   HF_CUDA(cudaMemsetAsync(J, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(K, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(b->counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
-  const PairSet ps = hf_pairset(b);
-  const KernelCommon kc = hf_kernel_common(ctx, o.flags);
-  long long total = 0;
-  // heaviest classes first
-  for (int c = HF_NCLASS - 1; c >= 0; --c) {
-    const EriClassOps& op = ctx->ops[c];
-    ClassWork& w64 = b->work64[c];
-    ClassWork& w32 = b->work32[c];
-    const MolJK one{D, J, K, b->nbf, 0};
-    if (w64.w.nitems > 0)
-      hf_jk_hi(op, o.flags)(w64.w, ps, kc, one, nullptr, launch_grid(ctx, hf_occ_hi(op, o.flags), w64.w.nitems), st);
-    if (w32.w.nitems > 0) op.jk32(w32.w, ps, kc, one, nullptr, launch_grid(ctx, op.occ32(), w32.w.nitems), st);
-    total += w64.nquartets + w32.nquartets;
-  }
-  HF_CUDA(cudaGetLastError());
-  symmetrize_jk<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(J, K, b->nbf);
-  HF_CUDA(cudaGetLastError());
-  if (nq) *nq = total;
-  return HF_OK;
+  return hf_jk_run(b, D, J, K, J, K, b->counters.ptr, o, st, nq, nullptr);
 }
 
 // Operations per primitive quartet outside the VRR: p+q, 1/sqrt, 1/(p+q),
@@ -581,6 +613,7 @@ extern "C" int hf_fock_jk_profiled(hf_basis* b, const double* D, double* J, doub
   hf_jk_opts o;
   hf_jk_opts_default(&o);
   if (opts) o = *opts;
+  if (!(o.schwarz_tau >= 0.0) || !(o.fp32_bound >= 0.0)) return hf_fail(HF_ERR_INVALID, "negative threshold");
   hf_ctx* ctx = b->ctx;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
@@ -590,37 +623,20 @@ extern "C" int hf_fock_jk_profiled(hf_basis* b, const double* D, double* J, doub
   HF_CUDA(cudaMemsetAsync(J, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(K, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(b->counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
-  const PairSet ps = hf_pairset(b);
-  const KernelCommon kc = hf_kernel_common(ctx, o.flags);
-  const MolJK one{D, J, K, b->nbf, 0};
-  cudaEvent_t ev[2 * HF_NCLASS + 1];
-  for (auto& e : ev) HF_CUDA(cudaEventCreate(&e));
-  int nev = 0;
-  int which[2 * HF_NCLASS];
-  HF_CUDA(cudaEventRecord(ev[nev++], st));
-  for (int c = HF_NCLASS - 1; c >= 0; --c) {
-    const EriClassOps& op = ctx->ops[c];
-    for (int r = 0; r < 2; ++r) {
-      ClassWork& w = r == 0 ? b->work64[c] : b->work32[c];
-      if (w.w.nitems <= 0) continue;
-      (r == 0 ? hf_jk_hi(op, o.flags) : op.jk32)(
-          w.w, ps, kc, one, nullptr, launch_grid(ctx, r == 0 ? hf_occ_hi(op, o.flags) : op.occ32(), w.w.nitems), st);
-      which[nev - 1] = 2 * c + r;
-      HF_CUDA(cudaEventRecord(ev[nev++], st));
+  JKClassTiming tm;
+  for (auto& e : tm.ev) HF_CUDA(cudaEventCreate(&e));
+  const int rc = hf_jk_run(b, D, J, K, J, K, b->counters.ptr, o, st, nullptr, &tm);
+  if (rc == HF_OK) {
+    HF_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < 2 * HF_NCLASS; ++k) class_ms[k] = 0.0;
+    for (int k = 0; k + 1 < tm.n; ++k) {
+      float ms = 0.f;
+      HF_CUDA(cudaEventElapsedTime(&ms, tm.ev[k], tm.ev[k + 1]));
+      class_ms[tm.which[k]] = ms;
     }
   }
-  HF_CUDA(cudaGetLastError());
-  symmetrize_jk<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(J, K, b->nbf);
-  HF_CUDA(cudaGetLastError());
-  HF_CUDA(cudaStreamSynchronize(st));
-  for (int k = 0; k < 2 * HF_NCLASS; ++k) class_ms[k] = 0.0;
-  for (int k = 0; k + 1 < nev; ++k) {
-    float ms = 0.f;
-    HF_CUDA(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
-    class_ms[which[k]] = ms;
-  }
-  for (auto& e : ev) cudaEventDestroy(e);
-  return HF_OK;
+  for (auto& e : tm.ev) cudaEventDestroy(e);
+  return rc;
 }
 
 extern "C" int hf_fock_jk(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts* opts) {
@@ -672,13 +688,16 @@ int hf_eri_tensor_device(hf_basis* b, double* G) {
   const KernelCommon kc = hf_kernel_common(ctx, 0);
   for (int c = 0; c < HF_NCLASS; ++c) {
     ClassWork& w = b->work64[c];
-    if (w.w.nitems > 0) ctx->ops[c].store(w.w, ps, kc, G, b->nbf, launch_grid(ctx, 4, w.w.nitems), st);
+    if (w.w.nitems > 0) ctx->ops[c].store(w.w, ps, kc, G, b->nbf, hf_launch_grid(ctx, 4, w.w.nitems), st);
   }
   HF_CUDA(cudaGetLastError());
   return HF_OK;
 }
 
-// J_ij = sum_kl G_ijkl D_kl and K_il = sum_jk G_ijkl D_jk: one warp per output element.
+// J_ij = sum_kl G_ijkl D_kl and K_il = sum_jk G_ijkl D_jk: one warp per output
+// element.  The tensor holds every permutation image of Eq. 5, so the K sum
+// reads (ip|xq) = (ip|qx): consecutive lanes take consecutive q in both sums,
+// and each warp reads n^2 contiguous doubles.
 __global__ void jk_stored_kernel(const double* __restrict__ G, const double* __restrict__ D, double* __restrict__ J,
                                  double* __restrict__ K, int n) {
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -692,7 +711,7 @@ __global__ void jk_stored_kernel(const double* __restrict__ G, const double* __r
   for (long long t = lane; t < nn; t += 32) {
     const int p = (int)(t / n), q = (int)(t % n);
     if (!isK) s += G[(((size_t)i * n + x) * n + p) * n + q] * D[(size_t)p * n + q];       // J_ix, (ix|pq) D_pq
-    else s += G[(((size_t)i * n + p) * n + q) * n + x] * D[(size_t)p * n + q];           // K_ix, (ip|qx) D_pq
+    else s += G[(((size_t)i * n + p) * n + x) * n + q] * D[(size_t)p * n + q];           // K_ix, (ip|xq) D_pq
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);

@@ -152,12 +152,21 @@ struct BoysSel<L, double> {
   }
 };
 template <int L>
+__device__ __forceinline__ void boys_df(df64 T, const float* __restrict__ tab, df64* F);
+
+template <int L>
 struct BoysSel<L, float> {
   // Reduced-precision quartets: F_m in FP64 (table + downward recursion),
-  // rounded to FP32 for the recurrences, unless boys_fp32 is set.
+  // rounded to FP32 for the recurrences; in df64 (same recursion, 48-bit
+  // significand) in the df64 tier; in FP32 when boys_fp32 is set.
   static __device__ __forceinline__ void eval(float T, const KernelCommon& kc, float* F) {
     if (kc.boys_fp32) {
       boys32<L>(T, kc.boys32, F);
+    } else if (kc.boys_df) {
+      df64 Fd[L + 1];
+      boys_df<L>(df64(T, 0.0f), kc.boysdf, Fd);
+#pragma unroll
+      for (int m = 0; m <= L; ++m) F[m] = __fadd_rn(Fd[m].hi, Fd[m].lo);
     } else {
       double Fd[L + 1];
       boys64<L>((double)T, kc.boys64, Fd);
@@ -209,21 +218,53 @@ __device__ __forceinline__ void contracted_vrr(const PairSet& ps, const KernelCo
 
 // ------------------------------------------------------------- df64 path
 // Boys in df64: grid T_i = i/16 (exact in FP32), x = T_i - T exact as a
-// two-term sum; F_m(T) = sum_{k<8} F_{m+k}(T_i) x^k/k! by Horner, the
-// terms k >= 5 (below 2^-30 of the sum, |x| <= 1/32) in FP32, k <= 4 in
-// df64.  For L >= 1: F_L that way, exp(-T) likewise (same table row, one
-// cache line), then the downward recursion in df64.  T >= BOYS_TMAX: F_0 = sqrt(pi)/2 T^{-1/2},
-// F_{m+1} = (2m+1)/(2T) F_m.
-__device__ __forceinline__ df64 boys_horner_df(const float* __restrict__ c, df64 x) {
-  const float4* c4 = reinterpret_cast<const float4*>(c);
-  const float4 q0 = __ldg(c4), q1 = __ldg(c4 + 1), q2 = __ldg(c4 + 2), q3 = __ldg(c4 + 3);
-  float g = __fmaf_rn(q3.x, x.hi, q2.w);  // c7 x + c6
-  g = __fmaf_rn(g, x.hi, q2.z);           // + c5
-  df64 f = df64(q2.x, q2.y) + df_mulf(x, g);
-  f = df_fma(x, f, df64(q1.z, q1.w));
-  f = df_fma(x, f, df64(q1.x, q1.y));
-  f = df_fma(x, f, df64(q0.z, q0.w));
-  return df_fma(x, f, df64(q0.x, q0.y));
+// two-term sum (|x| <= 1/32).  F_L(T) = sum_{k<8} F_{L+k}(T_i) x^k/k! by
+// Horner on the row's coefficients, the terms k >= 5 (below 2^-30 of the
+// sum) in FP32 and k <= 4 in df64.  For L >= 1 also exp(-T) =
+// exp(-T_i) e^x, with e^x = sum_{k<8} x^k/k! (truncation below 2^-55) by
+// Horner on constant coefficients, then the downward recursion in df64.
+// The row (16 floats, 64 bytes) comes in two 256-bit loads: per lane two
+// 32-byte sectors instead of one 16-byte load per coefficient pair.
+// T >= BOYS_TMAX: F_0 = sqrt(pi)/2 T^{-1/2}, F_{m+1} = (2m+1)/(2T) F_m.
+struct BoysRowDf {
+  float v[16];
+};
+
+__device__ __forceinline__ void ldg256(const float* __restrict__ p, float* v) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+      : "l"(p));
+}
+
+__device__ __forceinline__ BoysRowDf load_boys_row_df(const float* __restrict__ r) {
+  BoysRowDf q;
+  ldg256(r, q.v);
+  ldg256(r + 8, q.v + 8);
+  return q;
+}
+
+__device__ __forceinline__ df64 boys_horner_df(const BoysRowDf& q, df64 x) {
+  float g = __fmaf_rn(q.v[12], x.hi, q.v[11]);  // c7 x + c6
+  g = __fmaf_rn(g, x.hi, q.v[10]);              // + c5
+  df64 f = df64(q.v[8], q.v[9]) + df_mulf(x, g);
+  f = df_fma(x, f, df64(q.v[6], q.v[7]));
+  f = df_fma(x, f, df64(q.v[4], q.v[5]));
+  f = df_fma(x, f, df64(q.v[2], q.v[3]));
+  return df_fma(x, f, df64(q.v[0], q.v[1]));
+}
+
+// (hi, lo) of a double constant
+__device__ __forceinline__ constexpr df64 df_const(double v) { return df64((float)v, (float)(v - (double)(float)v)); }
+
+// e^x for |x| <= 1/32: terms k = 5..7 in FP32, k <= 4 in df64
+__device__ __forceinline__ df64 df_exp_small(df64 x) {
+  float g = __fmaf_rn(1.0f / 5040.0f, x.hi, 1.0f / 720.0f);
+  g = __fmaf_rn(g, x.hi, 1.0f / 120.0f);
+  df64 f = df_const(1.0 / 24.0) + df_mulf(x, g);
+  f = df_fma(x, f, df_const(1.0 / 6.0));
+  f = df_fma(x, f, df64(0.5f, 0.0f));
+  f = df_fma(x, f, df64(1.0f, 0.0f));
+  return df_fma(x, f, df64(1.0f, 0.0f));
 }
 
 // (hi, lo) of 1/(2m+1), m = 0..7
@@ -239,13 +280,10 @@ __device__ __forceinline__ void boys_df(df64 T, const float* __restrict__ tab, d
     const int i = __float2int_rn(T.hi * BOYSDF_INV_H);
     const float xh = __fsub_rn((float)i * (1.0f / BOYSDF_INV_H), T.hi);  // exact (Sterbenz)
     const df64 x = df64(xh, 0.0f) + df64(-T.lo, 0.0f);
-    if (L == 0) {
-      F[0] = boys_horner_df(tab + (size_t)i * BOYSDF_ROW, x);
-    } else {
-      // one 128-byte row holds both the F_L and the exp coefficients
-      const float* __restrict__ r = tab + ((size_t)L * BOYSDF_NGRID + i) * BOYSDF_ROW;
-      F[L] = boys_horner_df(r, x);
-      const df64 e = boys_horner_df(r + 16, x);
+    const BoysRowDf q = load_boys_row_df(tab + ((size_t)L * BOYSDF_NGRID + i) * BOYSDF_ROW);
+    F[L] = boys_horner_df(q, x);
+    if (L > 0) {
+      const df64 e = df64(q.v[14], q.v[15]) * df_exp_small(x);
       const df64 t2 = df_scale2(T, 2.0f);
 #pragma unroll
       for (int m = L - 1; m >= 0; --m) F[m] = (t2 * F[m + 1] + e) * df_inv_odd(m);
@@ -359,10 +397,11 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
       R CD[3] = {(R)ket.AB[0], (R)ket.AB[1], (R)ket.AB[2]};
       C::template hrr<R>(acc, I, AB, CD);
     }
-    const double* __restrict__ D = mjp ? mjp->D : one.D;
-    double* __restrict__ J = mjp ? mjp->J : one.J;
-    double* __restrict__ Kx = mjp ? mjp->K : one.K;
-    const int nbf = mjp ? mjp->nbf : one.nbf;
+    const MolJK& mo = mjp ? *mjp : one;
+    const double* __restrict__ Dj = mo.Dj ? mo.Dj : mo.D;
+    double* __restrict__ J = mo.J;
+    const int nbf = mo.nbf;
+    const int nspin = mo.D2 ? 2 : 1;
     double wdeg = active ? 1.0 : 0.0;
     if (bra.same) wdeg *= 0.5;
     if (ket.same) wdeg *= 0.5;
@@ -375,7 +414,7 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
     for (int c = 0; c < NC; ++c)
 #pragma unroll
       for (int d = 0; d < ND; ++d)
-        Dcd[c * ND + d] = active ? __ldg(D + (size_t)(c0 + c) * nbf + d0 + d) * comp_scale(C::LC, c) * comp_scale(C::LD, d) : 0.0;
+        Dcd[c * ND + d] = active ? __ldg(Dj + (size_t)(c0 + c) * nbf + d0 + d) * comp_scale(C::LC, c) * comp_scale(C::LD, d) : 0.0;
 #pragma unroll
     for (int a = 0; a < NA; ++a)
 #pragma unroll
@@ -394,7 +433,7 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
     for (int a = 0; a < NA; ++a)
 #pragma unroll
       for (int b = 0; b < NB; ++b)
-        Dab[a * NB + b] = __ldg(D + (size_t)(a0 + a) * nbf + b0 + b) * comp_scale(C::LA, a) * comp_scale(C::LB, b);
+        Dab[a * NB + b] = __ldg(Dj + (size_t)(a0 + a) * nbf + b0 + b) * comp_scale(C::LA, a) * comp_scale(C::LB, b);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -404,6 +443,11 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
         for (int ab = 0; ab < NA * NB; ++ab) s = fma((double)I[ab * NC * ND + c * ND + d], Dab[ab], s);
         atomicAdd(J + (size_t)(c0 + c) * nbf + d0 + d, s * wdeg * comp_scale(C::LC, c) * comp_scale(C::LD, d));
       }
+    // exchange of each spin: K from D, and K2 from D2 in two-spin builds
+#pragma unroll 1
+    for (int sp = 0; sp < nspin; ++sp) {
+    const double* __restrict__ D = sp ? mo.D2 : mo.D;
+    double* __restrict__ Kx = sp ? mo.K2 : mo.K;
     // K'_ac = w sum_bd I D_bd ;  K'_ad = w sum_bc I D_bc
     {
       double Dbd[NB * ND], Dbc[NB * NC];
@@ -472,6 +516,7 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
         }
       }
     }
+    }  // spin
   }
 }
 
@@ -671,20 +716,22 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
     }
     __syncwarp();
     // digestion: one output element per lane for each of the six contractions
-    const double* __restrict__ D = mjp ? mjp->D : one.D;
-    double* __restrict__ J = mjp ? mjp->J : one.J;
-    double* __restrict__ Kx = mjp ? mjp->K : one.K;
-    const int nbf = mjp ? mjp->nbf : one.nbf;
+    const MolJK& mo = mjp ? *mjp : one;
+    const double* __restrict__ Dj = mo.Dj ? mo.Dj : mo.D;
+    double* __restrict__ J = mo.J;
+    const int nbf = mo.nbf;
+    const int nspin = mo.D2 ? 2 : 1;
     double wdeg = 1.0;
     if (bra.same) wdeg *= 0.5;
     if (ket.same) wdeg *= 0.5;
     if (bp == kp) wdeg *= 0.5;
     const int a0 = bra.bfA, b0 = bra.bfB, c0 = ket.bfA, d0 = ket.bfB;
-    auto Dsc = [&](int r0, int lr, int i, int c0_, int lc, int j) {
-      const double dv = __ldg(D + (size_t)(r0 + i) * nbf + c0_ + j);
+    auto Dsc_of = [&](const double* __restrict__ Dm, int r0, int lr, int i, int c0_, int lc, int j) {
+      const double dv = __ldg(Dm + (size_t)(r0 + i) * nbf + c0_ + j);
       if constexpr (kPre) return dv;
       else return dv * comp_scale_rt(lr, i) * comp_scale_rt(lc, j);
     };
+    auto Dsc = [&](int r0, int lr, int i, int c0_, int lc, int j) { return Dsc_of(Dj, r0, lr, i, c0_, lc, j); };
     auto Iv = [&](int a, int b, int c, int d) {
       if constexpr (kPre) return Id[((a * NB + b) * NC + c) * ND + d];
       else return (double)I[((a * NB + b) * NC + c) * ND + d];
@@ -706,34 +753,40 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
         for (int b = 0; b < NB; ++b) acc2 = fma(Iv(a, b, c, d), Dsc(a0, C::LA, a, b0, C::LB, b), acc2);
       atomicAdd(J + (size_t)(c0 + c) * nbf + d0 + d, acc2 * wdeg * osc(C::LC, c, C::LD, d));
     }
+#pragma unroll 1
+    for (int sp = 0; sp < nspin; ++sp) {  // exchange of each spin: K from D, K2 from D2
+    const double* __restrict__ Dk = sp ? mo.D2 : mo.D;
+    double* __restrict__ Kx = sp ? mo.K2 : mo.K;
+    auto Dsk = [&](int r0, int lr, int i, int c0_, int lc, int j) { return Dsc_of(Dk, r0, lr, i, c0_, lc, j); };
     for (int o = lane; o < C::NA * NC; o += 32) {  // K'_ac = w sum_bd I D_bd
       const int a = o / NC, c = o % NC;
       double acc2 = 0.0;
       for (int b = 0; b < NB; ++b)
-        for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsc(b0, C::LB, b, d0, C::LD, d), acc2);
+        for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsk(b0, C::LB, b, d0, C::LD, d), acc2);
       atomicAdd(Kx + (size_t)(a0 + a) * nbf + c0 + c, acc2 * wdeg * osc(C::LA, a, C::LC, c));
     }
     for (int o = lane; o < C::NA * ND; o += 32) {  // K'_ad = w sum_bc I D_bc
       const int a = o / ND, d = o % ND;
       double acc2 = 0.0;
       for (int b = 0; b < NB; ++b)
-        for (int c = 0; c < NC; ++c) acc2 = fma(Iv(a, b, c, d), Dsc(b0, C::LB, b, c0, C::LC, c), acc2);
+        for (int c = 0; c < NC; ++c) acc2 = fma(Iv(a, b, c, d), Dsk(b0, C::LB, b, c0, C::LC, c), acc2);
       atomicAdd(Kx + (size_t)(a0 + a) * nbf + d0 + d, acc2 * wdeg * osc(C::LA, a, C::LD, d));
     }
     for (int o = lane; o < NB * NC; o += 32) {  // K'_bc = w sum_ad I D_ad
       const int b = o / NC, c = o % NC;
       double acc2 = 0.0;
       for (int a = 0; a < C::NA; ++a)
-        for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsc(a0, C::LA, a, d0, C::LD, d), acc2);
+        for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsk(a0, C::LA, a, d0, C::LD, d), acc2);
       atomicAdd(Kx + (size_t)(b0 + b) * nbf + c0 + c, acc2 * wdeg * osc(C::LB, b, C::LC, c));
     }
     for (int o = lane; o < NB * ND; o += 32) {  // K'_bd = w sum_ac I D_ac
       const int b = o / ND, d = o % ND;
       double acc2 = 0.0;
       for (int a = 0; a < C::NA; ++a)
-        for (int c = 0; c < NC; ++c) acc2 = fma(Iv(a, b, c, d), Dsc(a0, C::LA, a, c0, C::LC, c), acc2);
+        for (int c = 0; c < NC; ++c) acc2 = fma(Iv(a, b, c, d), Dsk(a0, C::LA, a, c0, C::LC, c), acc2);
       atomicAdd(Kx + (size_t)(b0 + b) * nbf + d0 + d, acc2 * wdeg * osc(C::LB, b, C::LD, d));
     }
+    }  // spin
     __syncwarp();
   }
 }
@@ -757,7 +810,7 @@ inline size_t coop_smem_bytes(int g) {
 
 template <class C, typename R>
 inline void coop_launch(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one,
-                        const MolJK* mols, int grid, cudaStream_t s) {
+                        const MolJK* mols, int grid, int threads, cudaStream_t s) {
   const int g = coop_group<C>();
   const size_t sm = coop_smem_bytes<C, R>(g);
   static bool attr = false;  // set once per process (same function on every device)
@@ -765,7 +818,9 @@ inline void coop_launch(const JKWork& w, const PairSet& ps, const KernelCommon& 
     cudaFuncSetAttribute(eri_jk_coop_kernel<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  eri_jk_coop_kernel<C, R><<<grid, 128, sm, s>>>(w, ps, kc, one, mols, g);
+  // shared memory per warp of the block (the attribute covers four warps)
+  const size_t used = sm / 4 * (size_t)(threads / 32);
+  eri_jk_coop_kernel<C, R><<<grid, threads, used, s>>>(w, ps, kc, one, mols, g);
 }
 
 template <class C, typename R>
@@ -863,11 +918,11 @@ __global__ void __launch_bounds__(128) eri_schwarz_kernel(const int* __restrict_
 #define HF_DEFINE_CLASS_LAUNCHERS(CLS)                                                                   \
   template <typename R>                                                                                  \
   static void launch_jkR_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one,  \
-                               const MolJK* mols, int grid, cudaStream_t s) {                            \
+                               const MolJK* mols, int grid, int threads, cudaStream_t s) {               \
     if constexpr (hfgen::CLS::COOP)                                                                      \
-      hfk::coop_launch<hfgen::CLS, R>(w, ps, kc, one, mols, grid, s);                                    \
+      hfk::coop_launch<hfgen::CLS, R>(w, ps, kc, one, mols, grid, threads, s);                           \
     else                                                                                                 \
-      hfk::eri_jk_kernel<hfgen::CLS, R><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                      \
+      hfk::eri_jk_kernel<hfgen::CLS, R><<<grid, threads, 0, s>>>(w, ps, kc, one, mols);                  \
   }                                                                                                      \
   template <typename R>                                                                                  \
   static int occR_##CLS() {                                                                              \
@@ -879,21 +934,21 @@ __global__ void __launch_bounds__(128) eri_schwarz_kernel(const int* __restrict_
     return n;                                                                                            \
   }                                                                                                      \
   static void launch_jk64_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one, \
-                                const MolJK* mols, int grid, cudaStream_t s) {                           \
-    launch_jkR_##CLS<double>(w, ps, kc, one, mols, grid, s);                                             \
+                                const MolJK* mols, int grid, int threads, cudaStream_t s) {              \
+    launch_jkR_##CLS<double>(w, ps, kc, one, mols, grid, threads, s);                                    \
   }                                                                                                      \
   static void launch_jk32_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one, \
-                                const MolJK* mols, int grid, cudaStream_t s) {                           \
-    launch_jkR_##CLS<float>(w, ps, kc, one, mols, grid, s);                                              \
+                                const MolJK* mols, int grid, int threads, cudaStream_t s) {              \
+    launch_jkR_##CLS<float>(w, ps, kc, one, mols, grid, threads, s);                                     \
   }                                                                                                      \
   static void launch_jkdf_##CLS(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const MolJK& one, \
-                                const MolJK* mols, int grid, cudaStream_t s) {                           \
+                                const MolJK* mols, int grid, int threads, cudaStream_t s) {              \
     if constexpr (hfgen::CLS::COOP)                                                                      \
-      hfk::coop_launch<hfgen::CLS, df64>(w, ps, kc, one, mols, grid, s);                                 \
+      hfk::coop_launch<hfgen::CLS, df64>(w, ps, kc, one, mols, grid, threads, s);                        \
     else if constexpr (hfgen::CLS::L <= HF_DF_LMAX)                                                      \
-      hfk::eri_jk_kernel<hfgen::CLS, df64><<<grid, 128, 0, s>>>(w, ps, kc, one, mols);                   \
+      hfk::eri_jk_kernel<hfgen::CLS, df64><<<grid, threads, 0, s>>>(w, ps, kc, one, mols);               \
     else                                                                                                 \
-      launch_jkR_##CLS<double>(w, ps, kc, one, mols, grid, s);                                           \
+      launch_jkR_##CLS<double>(w, ps, kc, one, mols, grid, threads, s);                                  \
   }                                                                                                      \
   static int occ_jkdf_##CLS() {                                                                          \
     int n = 0;                                                                                           \

@@ -19,11 +19,12 @@
 #define BOYS32_TERMS 5
 #define BOYS32_ROW 10
 // df64 table: grid T_i = i / 16 (exact in FP32), T < BOYS_TMAX; per row and
-// order 32 floats: Taylor coefficients c_k = F_{L+k}(T_i)/k!, k = 0..4 as
-// (hi, lo) pairs then k = 5..7 as floats, pad to 16; the same for exp(-T).
+// order 16 floats (64 bytes, read as two 256-bit loads): Taylor coefficients
+// c_k = F_{L+k}(T_i)/k!, k = 0..4 as (hi, lo) pairs, k = 5..7 as floats, one
+// pad, then exp(-T_i) as a (hi, lo) pair.
 #define BOYSDF_INV_H 16.0f
 #define BOYSDF_NGRID 962
-#define BOYSDF_ROW 32
+#define BOYSDF_ROW 16
 // thread-per-quartet classes with L = la+lb+lc+ld up to this have a df64
 // variant; the warp-cooperative classes (L >= 5) take df64 through the
 // generic cooperative kernel
@@ -60,7 +61,10 @@ struct PairSet {
 // One molecule of a launch: density and J/K outputs (device, nbf x nbf
 // row-major), its own pair data and ket lists (ket_off[Y] = start of pair
 // class Y in ketlist), and whether it takes part (inactive molecules'
-// work items are skipped).
+// work items are skipped).  Unrestricted (two-spin) builds set Dj (the
+// density J is built from, D^a + D^b; null = D), D2 and K2 (the second
+// spin's density and exchange): one integral evaluation then feeds J[Dj],
+// K[D] and K2[D2].
 struct MolJK {
   const double* D;
   double* J;
@@ -70,6 +74,9 @@ struct MolJK {
   PairSet ps;
   const int* ketlist;
   int ket_off[HF_NPAIRCLASS];
+  const double* Dj;
+  const double* D2;
+  double* K2;
 };
 
 struct KernelCommon {
@@ -77,6 +84,7 @@ struct KernelCommon {
   const float* boys32;
   int boys_fp32;  // evaluate F_m in FP32 for reduced-precision quartets
   const float* boysdf;
+  int boys_df;    // reduced-precision quartets take F_m from the df64 evaluation (df64 tier)
 };
 
 // Work list of one (class, precision) launch.  Entry e pairs bra pair
@@ -102,8 +110,10 @@ __host__ __device__ inline int class_index(int la, int lb, int lc, int ld) {
   return x * (x + 1) / 2 + y;
 }
 
-typedef void (*jk_launch_fn)(const JKWork&, const PairSet&, const KernelCommon&, const MolJK&, const MolJK*, int,
-                             cudaStream_t);
+// Class launch: grid blocks of `threads` threads (128 = four warps, or 32 =
+// one warp per block when a class has few work items) on a stream.
+typedef void (*jk_launch_fn)(const JKWork&, const PairSet&, const KernelCommon&, const MolJK&, const MolJK*, int grid,
+                             int threads, cudaStream_t);
 typedef void (*store_launch_fn)(const JKWork&, const PairSet&, const KernelCommon&, double*, int, int, cudaStream_t);
 typedef void (*schwarz_launch_fn)(const int*, int, const PairSet&, const KernelCommon&, double*, cudaStream_t);
 typedef int (*occ_fn)();

@@ -127,8 +127,13 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound);
 inline PairSet hf_pairset(const hf_basis* b) {
   return PairSet{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr, b->primdf.ptr};
 }
+// Boys function of the reduced-precision (FP32) quartets: FP32 with
+// HF_JK_FP32_BOYS; else df64 in the df64 tier (the tier's stand-in for FP64);
+// else FP64.
 inline KernelCommon hf_kernel_common(const hf_ctx* c, unsigned jk_flags) {
-  return KernelCommon{c->boys64, c->boys32, (jk_flags & HF_JK_FP32_BOYS) ? 1 : 0, c->boysdf};
+  const int f32 = (jk_flags & HF_JK_FP32_BOYS) ? 1 : 0;
+  const int df = (!f32 && (jk_flags & HF_JK_DF64)) ? 1 : 0;
+  return KernelCommon{c->boys64, c->boys32, f32, c->boysdf, df};
 }
 // launcher for the higher-precision work of a class: df64 when requested
 inline jk_launch_fn hf_jk_hi(const EriClassOps& op, unsigned jk_flags) {
@@ -140,6 +145,32 @@ inline int hf_occ_hi(const EriClassOps& op, unsigned jk_flags) {
 int hf_basis_one_electron(hf_basis* b);  // fills b->S, T, V
 int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts& o,
                       long long* nquartets);
+// Grid of a persistent class launch: enough blocks of 4 warps for the work
+// items, at most occ resident blocks on every SM.
+int hf_launch_grid(hf_ctx* ctx, int occ, int nitems);
+// Shape of a class launch of nitems work items, occ resident 4-warp blocks
+// per SM (at most cap_per_sm when cap_per_sm > 0).  A class with at least
+// as many items as resident warps runs persistent 4-warp blocks that pull
+// items from the counter; a smaller one runs one-warp blocks, one per item,
+// so the few items (each a long serial primitive loop) spread over all SMs
+// instead of filling the four warps of the first few blocks.
+struct LaunchShape {
+  int grid, threads;
+};
+LaunchShape hf_launch_shape(const hf_ctx* ctx, int occ, int nitems, int cap_per_sm = 0);
+// CUDA events around each class launch of one J/K build (hf_fock_jk_profiled).
+struct JKClassTiming {
+  cudaEvent_t ev[2 * HF_NCLASS + 1];
+  int which[2 * HF_NCLASS];
+  int n = 0;
+};
+// The class kernels of one J/K build of b on stream st, for work lists
+// already prepared for o: accumulates into Jp, Kp (zeroed by the caller)
+// with the work-item counters at counters[0 .. 2*HF_NCLASS) (zeroed by the
+// caller), then writes J = 2 (Jp + Jp^T), K = Kp + Kp^T (J == Jp and K == Kp
+// for in place).  df64 and FP32 tiers as o.flags says.
+int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, double* K, int* counters,
+              const hf_jk_opts& o, cudaStream_t st, long long* nquartets, JKClassTiming* timing);
 int hf_boys_tables(hf_ctx* ctx);
 int hf_eri_tensor_device(hf_basis* b, double* G);
 int hf_jk_stored_device(hf_basis* b, const double* G, const double* D, double* J, double* K);

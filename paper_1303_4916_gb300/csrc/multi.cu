@@ -13,10 +13,12 @@ __global__ void zero_jk_batch(const MolJK* __restrict__ mols) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nn; t += (size_t)gridDim.x * blockDim.x) {
     m.J[t] = 0.0;
     m.K[t] = 0.0;
+    if (m.K2) m.K2[t] = 0.0;
   }
 }
 
-// J = 2 (J' + J'^T), K = K' + K'^T in place for every active molecule.
+// J = 2 (J' + J'^T), K = K' + K'^T (and K2 likewise) in place for every
+// active molecule.
 __global__ void symmetrize_jk_batch(const MolJK* __restrict__ mols) {
   const MolJK m = mols[blockIdx.y];
   if (!m.active) return;
@@ -32,6 +34,11 @@ __global__ void symmetrize_jk_batch(const MolJK* __restrict__ mols) {
     const double sk = m.K[ij] + m.K[ji];
     m.K[ij] = sk;
     m.K[ji] = sk;
+    if (m.K2) {
+      const double s2 = m.K2[ij] + m.K2[ji];
+      m.K2[ij] = s2;
+      m.K2[ji] = s2;
+    }
   }
 }
 
@@ -152,10 +159,9 @@ int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
       if (wk.nitems <= 0) continue;
       any = true;
       const int occ = std::max(r == 0 ? hf_occ_hi(op, jk_flags) : op.occ32(), 1);
-      const int per_sm = grid_scale[cls] > 0 ? std::min(occ, grid_scale[cls]) : occ;
-      const int grid = std::max(1, std::min((wk.nitems + 3) / 4, per_sm * ctx->num_sms));
+      const LaunchShape sh = hf_launch_shape(ctx, occ, wk.nitems, grid_scale[cls]);
       cudaStream_t ls = fork ? ctx->side[nlaunch++ % hf_ctx::kSide] : st;
-      (r == 0 ? hf_jk_hi(op, jk_flags) : op.jk32)(wk, none, kc, one, table.ptr, grid, ls);
+      (r == 0 ? hf_jk_hi(op, jk_flags) : op.jk32)(wk, none, kc, one, table.ptr, sh.grid, sh.threads, ls);
     }
     if (class_ms && any) {
       HF_CUDA(cudaEventRecord(ev[1], st));

@@ -38,7 +38,10 @@ namespace {
 std::mutex g_setup_mu;
 double* g_scratch_addr[256] = {};
 
-// Device address of the static array for the current device (looked up once).
+// Device address of the static array for the current device (looked up once
+// per device and kept for the life of the process; a cudaDeviceReset of that
+// device unloads the module and leaves the kept address stale, so the entry
+// point must not be used after one).
 int noalloc_scratch(int device, double** out) {
   if (device < 0 || device >= 256) return hf_fail(HF_ERR_INVALID, "device index %d", device);
   std::lock_guard<std::mutex> lk(g_setup_mu);
@@ -53,17 +56,6 @@ int noalloc_scratch(int device, double** out) {
   return HF_OK;
 }
 
-// J = 2 (J' + J'^T), K = K' + K'^T from the scratch accumulators into the outputs.
-__global__ void noalloc_finish(const double* __restrict__ Jp, const double* __restrict__ Kp, double* __restrict__ J,
-                               double* __restrict__ K, int n) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)n * n) return;
-  const int i = (int)(t / n), j = (int)(t % n);
-  const size_t ij = (size_t)i * n + j, ji = (size_t)j * n + i;
-  J[ij] = 2.0 * (Jp[ij] + Jp[ji]);
-  K[ij] = Kp[ij] + Kp[ji];
-}
-
 }  // namespace
 
 extern "C" int hf_fock_jk_noalloc(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts* opts) {
@@ -71,6 +63,7 @@ extern "C" int hf_fock_jk_noalloc(hf_basis* b, const double* D, double* J, doubl
   hf_jk_opts o;
   hf_jk_opts_default(&o);
   if (opts) o = *opts;
+  if (!(o.schwarz_tau >= 0.0) || !(o.fp32_bound >= 0.0)) return hf_fail(HF_ERR_INVALID, "negative threshold");
   if (o.flags & HF_JK_HOST)
     return hf_fail(HF_ERR_INVALID, "hf_fock_jk_noalloc: device pointers only (HF_JK_HOST needs staging buffers)");
   const int n = b->nbf;
@@ -95,25 +88,9 @@ extern "C" int hf_fock_jk_noalloc(hf_basis* b, const double* D, double* J, doubl
   HF_CUDA(cudaMemsetAsync(Jp, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(Kp, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 2 * HF_NCLASS, st));
-  PairSet ps{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr};
-  KernelCommon kc{ctx->boys64, ctx->boys32, (o.flags & HF_JK_FP32_BOYS) ? 1 : 0};
-  const MolJK one{D, Jp, Kp, n, 0};
-  for (int c = HF_NCLASS - 1; c >= 0; --c) {
-    const EriClassOps& op = ctx->ops[c];
-    for (int r = 0; r < 2; ++r) {
-      const ClassWork& cw = r == 0 ? b->work64[c] : b->work32[c];
-      if (cw.w.nitems <= 0) continue;
-      JKWork w = cw.w;
-      w.counter = counters + 2 * c + r;
-      const int occ = r == 0 ? op.occ64() : op.occ32();
-      const int items_grid = (w.nitems + 3) / 4;
-      const int cap = (occ > 0 ? occ : 1) * ctx->num_sms;
-      (r == 0 ? op.jk64 : op.jk32)(w, ps, kc, one, nullptr, items_grid < cap ? items_grid : cap, st);
-    }
-  }
-  HF_CUDA(cudaGetLastError());
-  noalloc_finish<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Jp, Kp, J, K, n);
-  HF_CUDA(cudaGetLastError());
+  // the same class launches, precision tiers and symmetrisation as
+  // hf_fock_jk, out of place from the static accumulators into J and K
+  HF_CHECK(hf_jk_run(b, D, Jp, Kp, J, K, counters, o, st, nullptr, nullptr));
   HF_CUDA(cudaStreamSynchronize(st));
   return HF_OK;
 }

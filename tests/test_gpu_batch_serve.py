@@ -94,6 +94,52 @@ def test_serve_mix_equals_alone(ctx, hf):
     srv.close()
 
 
+# Served molecules whose oracle SCF takes about a second on the host: s+p
+# ones and s+p+d ones with one heavy atom (so d shells take part).
+SERVED_ORACLE = [(3, 51, "sp"), (5, 52, "sp"), (2, 101, "spd"), (3, 100, "spd"), (3, 103, "spd"), (2, 104, "spd")]
+
+
+@pytest.fixture(scope="module")
+def served_oracle():
+    mols = [lattice_molecule(n, s, r) for n, s, r in SERVED_ORACLE]
+    ref = [oracle.rhf(m, max_iter=128, e_tol=1e-10, diis_size=8, tau=1e-12, nthreads=oracle.oracle_threads())
+           for m in mols]
+    assert all(r.converged for r in ref)
+    return mols, [r.energy for r in ref]
+
+
+@pytest.mark.parametrize("tier", ["fp64", "df64"])
+def test_serve_energies_match_oracle(ctx, hf, served_oracle, tier):
+    """Served SCF energies against the CPU oracle's RHF (not against the GPU's
+    own single-molecule solve), in plain FP64 and in the df64 tier, with later
+    requests arriving while earlier ones are on the GPU."""
+    mols, e_ref = served_oracle
+    srv = hf.Server(ctx, max_active=3, max_iter=128, e_tol=1e-10, diis_size=8, df64=(tier == "df64"))
+    tickets = [srv.submit(m) for m in mols[:3]]
+    time.sleep(0.05)
+    tickets += [srv.submit(m) for m in mols[3:]]
+    srv.drain(600)
+    results = [srv.poll(t) for t in tickets]
+    srv.close()
+    for (n, s, r), res, e in zip(SERVED_ORACLE, results, e_ref):
+        assert res.status == 0 and res.converged, (n, s, r)
+        assert abs(res.energy - e) <= E_TOL, (n, s, r, res.energy, e)
+
+
+def test_serve_drain_times_out_on_the_host(ctx, hf):
+    """A drain whose limit runs out while work is still on the GPU returns
+    HF_ERR_TIMEOUT (a host-side wait; the device work is untouched) and the
+    server keeps going: a later drain completes the request."""
+    from paper_1303_4916_gb300 import _abi
+    srv = hf.Server(ctx, max_active=1)
+    t = srv.submit(lattice_molecule(20, 5, "sp"))
+    assert hf.load().hf_serve_drain(srv._h, 1e-3) == _abi.HF_ERR_TIMEOUT
+    srv.drain(600)
+    r = srv.poll(t)
+    assert r.status == 0 and r.converged
+    srv.close()
+
+
 def test_serve_queue_limits(ctx, hf):
     from paper_1303_4916_gb300 import _abi
     srv = hf.Server(ctx, max_active=1, queue_capacity=2)
