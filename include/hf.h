@@ -160,11 +160,12 @@ void hf_ctx_inject_alloc_failure(hf_ctx* ctx, int n);
  * coefficients (Eq. 1), shell-pair data (Gaussian product centres and
  * prefactors per primitive pair), Schwarz factors Q_ab and the
  * class-bucketed quartet work lists.  All input arrays are host memory and
- * are copied.  n_electrons must be even (closed shell).
+ * are copied.  n_electrons >= 0 is the count the closed-shell calls use
+ * (hf_scf_solve and hf_scf_solve_batch return HF_ERR_ODD_ELECTRONS for an
+ * odd one; hf_uhf_solve takes its own spin counts).
  * Errors: HF_ERR_INVALID (also a shell with more than HF_MAX_NPRIM
  * primitives, a contraction of zero norm, two charged atoms at one point),
- * HF_ERR_UNSUPPORTED_L (l > HF_LMAX), HF_ERR_ODD_ELECTRONS, HF_ERR_OOM,
- * HF_ERR_CUDA. */
+ * HF_ERR_UNSUPPORTED_L (l > HF_LMAX), HF_ERR_OOM, HF_ERR_CUDA. */
 int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, const hf_shell* shells,
                     int nshell, const double* exps, const double* coefs, int n_electrons,
                     hf_basis** out);
@@ -253,8 +254,56 @@ int hf_jk_stored(hf_basis* b, const double* G, const double* D, double* J, doubl
  * DIIS with error F D S - S D F, until |dE| <= e_tol.  The J/K phase of an
  * iteration is captured once into a CUDA graph and replayed.
  * Returns HF_ERR_NOT_CONVERGED (result filled) after max_iter,
- * HF_ERR_LINDEP if lambda_min(S) < 1e-10. */
+ * HF_ERR_LINDEP if lambda_min(S) < 1e-10, HF_ERR_ODD_ELECTRONS for an odd
+ * electron count of the basis. */
 int hf_scf_solve(hf_basis* b, const hf_scf_opts* opts, hf_scf_result* res);
+
+/* ---------------------------------------------------------------- unrestricted */
+
+/* Unrestricted (two-spin) J/K, the contraction of the J/K equation
+ * (Sec. "Technical details") as the paper's UHF calculations need it:
+ * J = J[Da + Db], Ka = K[Da], Kb = K[Db], all three from one evaluation of
+ * the integrals of Eq. 5.  Da, Db, J, Ka, Kb are nbf x nbf DEVICE pointers
+ * (symmetric densities; the outputs are overwritten).  opts as for
+ * hf_fock_jk except HF_JK_HOST (HF_ERR_INVALID).  The basis keeps one
+ * nbf x nbf device buffer for Da + Db after the first call.  Errors as
+ * hf_fock_jk. */
+int hf_fock_jk_uhf(hf_basis* b, const double* Da, const double* Db, double* J, double* Ka, double* Kb,
+                   const hf_jk_opts* opts);
+
+/* UHF result.  Da, Db (nbf x nbf) and eps_a, eps_b (nbf) may point at
+ * DEVICE buffers to receive the converged spin densities and orbital
+ * energies; NULL skips an output. */
+typedef struct {
+    double energy;       /* E = (1/2) sum_s Tr[D^s (H + F^s)] + E_nuc */
+    double e_elec;
+    double e_nuc;
+    double delta_e;      /* |E_k - E_{k-1}| at the last iteration */
+    double diis_error;   /* max |F^s D^s S - S D^s F^s| over both spins */
+    double s2;           /* <S^2> of the determinant */
+    int iterations;
+    int converged;
+    long long fock_builds;
+    long long quartets;
+    double seconds;
+    double* Da;
+    double* Db;
+    double* eps_a;
+    double* eps_b;
+} hf_uhf_result;
+
+/* Unrestricted HF, the form of the paper's test calculations (Sec. "Tests",
+ * runs RUN1 and RUN7), by the Pople-Nesbet equations as Szabo-Ostlund state
+ * them: per spin s with n_s electrons D^s = C^s_occ C^s_occ^T and
+ * F^s = H + J[D^a + D^b] - K[D^s]; Loewdin X, core guess F^a = F^b = H;
+ * DIIS (Pulay) on the stacked errors F^s D^s S - S D^s F^s with one set of
+ * coefficients for both spins; stop at |E_k - E_{k-1}| <= e_tol.  J, K^a,
+ * K^b of an iteration come from one integral evaluation (hf_fock_jk_uhf),
+ * replayed from a CUDA graph.  nbf >= n_alpha >= n_beta >= 0; the basis's
+ * n_electrons is not used.  opts: as hf_scf_solve without
+ * HF_SCF_STORED_ERI and D0 (HF_ERR_INVALID).  Returns HF_ERR_NOT_CONVERGED
+ * (result filled) after max_iter, HF_ERR_LINDEP as hf_scf_solve. */
+int hf_uhf_solve(hf_basis* b, int n_alpha, int n_beta, const hf_scf_opts* opts, hf_uhf_result* res);
 
 /* ---------------------------------------------------------------- batch */
 

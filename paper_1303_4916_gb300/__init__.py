@@ -1,7 +1,7 @@
 """GB300 (sm_103a) library for the closed-shell Hartree-Fock two-electron hot
 path: contracted Cartesian Gaussian ERIs (Eq. 5) contracted into J and K
-(the J/K equation of Sec. "Technical details"), the RHF iteration around
-it, and batched / continuous-batching serving forms.
+(the J/K equation of Sec. "Technical details"), the RHF and UHF iterations
+around it, and batched / continuous-batching serving forms.
 
 The compute lives in ``libhf.so`` (CUDA, C ABI in ``include/hf.h``); this
 package is its ctypes binding.  The first call loads the library and raises
@@ -14,6 +14,7 @@ from .api import (  # noqa: F401
     hf_ctx_create,
     hf_eri_tensor,
     hf_fock_jk,
+    hf_fock_jk_uhf,
     hf_fock_jk_noalloc,
     hf_jk_stored,
     hf_one_electron,
@@ -25,11 +26,13 @@ from .api import (  # noqa: F401
     hf_serve_drain,
     hf_serve_poll,
     hf_serve_submit,
+    hf_uhf_solve,
     Basis,
     Context,
     HFError,
     SCFResult,
     Server,
+    UHFResult,
     hf_jk_opts_default,
     hf_scf_opts_default,
     jk_opts,

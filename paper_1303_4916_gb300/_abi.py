@@ -61,6 +61,14 @@ class hf_scf_result(C.Structure):
                 ("F1", C.c_void_p)]
 
 
+class hf_uhf_result(C.Structure):
+    _fields_ = [("energy", C.c_double), ("e_elec", C.c_double), ("e_nuc", C.c_double),
+                ("delta_e", C.c_double), ("diis_error", C.c_double), ("s2", C.c_double),
+                ("iterations", C.c_int), ("converged", C.c_int), ("fock_builds", C.c_longlong),
+                ("quartets", C.c_longlong), ("seconds", C.c_double),
+                ("Da", C.c_void_p), ("Db", C.c_void_p), ("eps_a", C.c_void_p), ("eps_b", C.c_void_p)]
+
+
 class hf_class_stats(C.Structure):
     _fields_ = [("la", C.c_int), ("lb", C.c_int), ("lc", C.c_int), ("ld", C.c_int),
                 ("vrr_flops", C.c_int), ("hrr_flops", C.c_int), ("prim_flops", C.c_int),
@@ -120,6 +128,8 @@ SIGNATURES = {
     "hf_eri_tensor": (I, [P, P]),
     "hf_jk_stored": (I, [P, P, P, P, P]),
     "hf_scf_solve": (I, [P, C.POINTER(hf_scf_opts), C.POINTER(hf_scf_result)]),
+    "hf_fock_jk_uhf": (I, [P, P, P, P, P, P, C.POINTER(hf_jk_opts)]),
+    "hf_uhf_solve": (I, [P, I, I, C.POINTER(hf_scf_opts), C.POINTER(hf_uhf_result)]),
     "hf_scf_solve_batch": (I, [C.POINTER(P), I, C.POINTER(hf_scf_opts), C.POINTER(hf_scf_result),
                                C.POINTER(I)]),
     "hf_serve_opts_default": (None, [C.POINTER(hf_serve_opts)]),

@@ -265,6 +265,58 @@ class Basis:
                          converged=bool(r.converged), fock_builds=r.fock_builds, quartets=r.quartets,
                          seconds=r.seconds, tensors=out)
 
+    def fock_jk_uhf(self, Da, Db, opts: Optional[hf_jk_opts] = None):
+        """J[Da + Db], K[Da], K[Db] (CUDA tensors) from one integral evaluation."""
+        import torch
+        J, Ka, Kb = torch.empty_like(Da), torch.empty_like(Da), torch.empty_like(Da)
+        _check(_lib().hf_fock_jk_uhf(self._h, _ptr(Da), _ptr(Db), _ptr(J), _ptr(Ka), _ptr(Kb),
+                                     C.byref(opts) if opts else None), "hf_fock_jk_uhf")
+        return J, Ka, Kb
+
+    def uhf(self, n_alpha: int, n_beta: int, max_iter: int = 128, e_tol: float = 1e-8, diis_size: int = 8,
+            schwarz_tau: float = 1e-12, fp32_bound: float = 0.0, df64: bool = False, outputs: bool = True,
+            allow_unconverged: bool = True):
+        import torch
+        o = hf_scf_opts_default()
+        o.max_iter = max_iter
+        o.e_tol = e_tol
+        o.diis_size = diis_size
+        o.jk = jk_opts(schwarz_tau, fp32_bound, df64=df64)
+        r = _abi.hf_uhf_result()
+        out = {}
+        if outputs:
+            n = self.nbf
+            dev = torch.device("cuda", self.ctx.device)
+            for k in ("Da", "Db"):
+                out[k] = torch.empty((n, n), dtype=torch.float64, device=dev)
+                setattr(r, k, out[k].data_ptr())
+            for k in ("eps_a", "eps_b"):
+                out[k] = torch.empty((n,), dtype=torch.float64, device=dev)
+                setattr(r, k, out[k].data_ptr())
+        ok = (_abi.HF_OK, _abi.HF_ERR_NOT_CONVERGED) if allow_unconverged else (_abi.HF_OK,)
+        rc = _check(_lib().hf_uhf_solve(self._h, int(n_alpha), int(n_beta), C.byref(o), C.byref(r)),
+                    "hf_uhf_solve", ok)
+        return UHFResult(rc=rc, energy=r.energy, e_elec=r.e_elec, e_nuc=r.e_nuc, delta_e=r.delta_e,
+                         diis_error=r.diis_error, s2=r.s2, iterations=r.iterations, converged=bool(r.converged),
+                         fock_builds=r.fock_builds, quartets=r.quartets, seconds=r.seconds, tensors=out)
+
+
+@dataclass
+class UHFResult:
+    rc: int
+    energy: float
+    e_elec: float
+    e_nuc: float
+    delta_e: float
+    diis_error: float
+    s2: float
+    iterations: int
+    converged: bool
+    fock_builds: int
+    quartets: int
+    seconds: float
+    tensors: dict
+
 
 @dataclass
 class SCFResult:
@@ -407,6 +459,14 @@ def hf_jk_stored(basis: Basis, G, D):
 
 def hf_scf_solve(basis: Basis, **kw) -> SCFResult:
     return basis.scf(**kw)
+
+
+def hf_uhf_solve(basis: Basis, n_alpha: int, n_beta: int, **kw) -> UHFResult:
+    return basis.uhf(n_alpha, n_beta, **kw)
+
+
+def hf_fock_jk_uhf(basis: Basis, Da, Db, opts: Optional[hf_jk_opts] = None):
+    return basis.fock_jk_uhf(Da, Db, opts)
 
 
 def hf_scf_solve_batch(bases, **kw):

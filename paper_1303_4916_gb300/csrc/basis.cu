@@ -134,7 +134,6 @@ extern "C" int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, con
   if (!ctx || !atoms || !shells || !exps || !coefs || natom <= 0 || nshell <= 0)
     return hf_fail(HF_ERR_INVALID, "hf_basis_create: null or empty input");
   if (n_electrons < 0) return hf_fail(HF_ERR_INVALID, "negative electron count");
-  if (n_electrons % 2) return hf_fail(HF_ERR_ODD_ELECTRONS, "closed-shell RHF needs an even electron count (%d)", n_electrons);
   int nprim = 0, nbf = 0, lmax = 0;
   for (int s = 0; s < nshell; ++s) {
     const hf_shell& sh = shells[s];
@@ -362,11 +361,11 @@ extern "C" int hf_basis_nshell(const hf_basis* b) { return b ? b->nshell : 0; }
 extern "C" size_t hf_basis_device_bytes(const hf_basis* b) {
   if (!b) return 0;
   size_t s = b->prim64.bytes() + b->prim32.bytes() + b->primdf.bytes() + b->pinfo.bytes() + b->Q.bytes() + b->ketlist.bytes() +
-             b->counters.bytes() + b->hD.bytes() + b->hJ.bytes() + b->hK.bytes() + b->S.bytes() + b->T.bytes() +
+             b->counters.bytes() + b->hD.bytes() + b->hJ.bytes() + b->hK.bytes() + b->Dsum.bytes() + b->S.bytes() + b->T.bytes() +
              b->V.bytes();
   for (int c = 0; c < HF_NCLASS; ++c)
     for (const ClassWork* w : {&b->work64[c], &b->work32[c]})
-      s += w->bra.bytes() + w->kbeg.bytes() + w->kend.bytes() + w->ioff.bytes();
+      s += w->bra.bytes() + w->kbeg.bytes() + w->kend.bytes() + w->ioff.bytes() + w->nsplit.bytes();
   return s;
 }
 
@@ -401,7 +400,7 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
       const int yb = b->class_begin[Y];
       const std::vector<int>& bk = b->buckets[Y];
       const int chunk = ctx->ops[cls].chunk;
-      std::vector<int> bra[2], kb[2], ke[2], io[2];
+      std::vector<int> bra[2], kb[2], ke[2], io[2], sp[2];
       long long nq[2] = {0, 0};
       io[0].push_back(0);
       io[1].push_back(0);
@@ -427,16 +426,45 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
           for (int r = 0; r < 2; ++r) {
             const int cnt = hi_[r] - lo_[r];
             if (cnt <= 0) continue;
-            // item offsets are int on the device: stop before the running
-            // sum could pass the limit (checked in 64 bits, per entry)
-            const long long next = (long long)io[r].back() + (cnt + chunk - 1) / chunk;
-            if (next > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "class %d: too many work items", cls);
             bra[r].push_back(pi);
             kb[r].push_back(lo_[r]);
             ke[r].push_back(hi_[r]);
-            io[r].push_back((int)next);
             nq[r] += cnt;
           }
+        }
+      }
+      // Item split along the primitive loop.  A class whose work is small
+      // next to the GPU is bound by its longest items (a lane walks up to
+      // nb x nk primitive quartets in series), so when the class's work per
+      // resident warp is below an item's length, the long items are cut
+      // into parts of about that length: bra primitive pairs for the
+      // thread-per-quartet kernels, primitive quartets (whole rounds of 32)
+      // for the warp-cooperative ones.  Large workloads are not split.
+      const int yb_ = b->class_begin[Y];
+      for (int r = 0; r < 2; ++r) {
+        const size_t ne = bra[r].size();
+        std::vector<long long> len(ne);
+        long long work = 0;
+        for (size_t e = 0; e < ne; ++e) {
+          const long long nbp = b->nprim_sig_h[bra[r][e]];
+          const long long nkp = b->nprim_sig_h[b->ketlist_h[yb_ + kb[r][e]]];  // uniform inside a bucket
+          len[e] = nbp * nkp;  // primitive quartets per lane (per warp for the cooperative kernels)
+          work += len[e] * ((ke[r][e] - kb[r][e] + chunk - 1) / chunk);
+        }
+        const long long warps = 16LL * ctx->num_sms;
+        const long long floor_len = chunk == 1 ? 64 : 16;
+        const long long target = std::max(floor_len, work / std::max(1LL, warps));
+        sp[r].resize(ne);
+        for (size_t e = 0; e < ne; ++e) {
+          const long long nbp = b->nprim_sig_h[bra[r][e]];
+          long long parts = (len[e] + target - 1) / target;
+          parts = std::min(parts, chunk == 1 ? std::max(1LL, (len[e] + 31) / 32) : std::max(1LL, nbp));
+          sp[r][e] = (int)std::max(1LL, parts);
+          // item offsets are int on the device: checked in 64 bits, per entry
+          const long long next =
+              (long long)io[r].back() + (long long)((ke[r][e] - kb[r][e] + chunk - 1) / chunk) * sp[r][e];
+          if (next > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "class %d: too many work items", cls);
+          io[r].push_back((int)next);
         }
       }
       for (int r = 0; r < 2; ++r) {
@@ -446,11 +474,13 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
         HF_CHECK(w.kbeg.alloc(ctx, nb));
         HF_CHECK(w.kend.alloc(ctx, nb));
         HF_CHECK(w.ioff.alloc(ctx, nb + 1));
+        HF_CHECK(w.nsplit.alloc(ctx, nb));
         if (nb > 0) {
           HF_CUDA(cudaMemcpyAsync(w.bra.ptr, bra[r].data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
           HF_CUDA(cudaMemcpyAsync(w.kbeg.ptr, kb[r].data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
           HF_CUDA(cudaMemcpyAsync(w.kend.ptr, ke[r].data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
           HF_CUDA(cudaMemcpyAsync(w.ioff.ptr, io[r].data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
+          HF_CUDA(cudaMemcpyAsync(w.nsplit.ptr, sp[r].data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
         }
         w.w.bra = w.bra.ptr;
         w.w.ket = b->ketlist.ptr + yb;
@@ -458,6 +488,7 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
         w.w.kend = w.kend.ptr;
         w.w.ioff = w.ioff.ptr;
         w.w.mol = nullptr;
+        w.w.nsplit = w.nsplit.ptr;
         w.w.nbra = nb;
         w.w.nitems = io[r].back();
         w.w.counter = b->counters.ptr + 2 * cls + r;
@@ -466,6 +497,7 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
         w.bra_h = std::move(bra[r]);
         w.kbeg_h = std::move(kb[r]);
         w.kend_h = std::move(ke[r]);
+        w.nsplit_h = std::move(sp[r]);
       }
     }
   // the host vectors above are consumed by the async copies: wait for them
@@ -503,17 +535,21 @@ int hf_launch_grid(hf_ctx* ctx, int occ, int nitems) {
 
 LaunchShape hf_launch_shape(const hf_ctx* ctx, int occ, int nitems, int cap_per_sm) {
   const int per_sm = std::max(1, cap_per_sm > 0 ? std::min(occ, cap_per_sm) : occ);
-  const long long slots = 4LL * per_sm * ctx->num_sms;  // resident warps
-  if (nitems >= slots) return LaunchShape{std::max(1, per_sm * ctx->num_sms), 128};
-  return LaunchShape{std::max(1, nitems), 32};
+  const int g = (int)std::min<long long>((nitems + 3LL) / 4, (long long)per_sm * ctx->num_sms);
+  return LaunchShape{std::max(1, g), 128};
 }
 
 int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, double* K, int* counters,
-              const hf_jk_opts& o, cudaStream_t st, long long* nq, JKClassTiming* timing) {
+              const hf_jk_opts& o, cudaStream_t st, long long* nq, JKClassTiming* timing, const JKSpin* spin) {
   hf_ctx* ctx = b->ctx;
   const PairSet ps = hf_pairset(b);
   const KernelCommon kc = hf_kernel_common(ctx, o.flags);
-  const MolJK one{D, Jp, Kp, b->nbf, 0};
+  MolJK one{D, Jp, Kp, b->nbf, 0};
+  if (spin) {
+    one.Dj = spin->Dj;
+    one.D2 = spin->D2;
+    one.K2 = spin->K2;
+  }
   long long total = 0;
   if (timing) {
     timing->n = 0;
@@ -540,7 +576,8 @@ int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, d
   }
   HF_CUDA(cudaGetLastError());
   const size_t nn = (size_t)b->nbf * b->nbf;
-  symmetrize_jk<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Jp, Kp, J, K, nullptr, nullptr, b->nbf);
+  double* K2 = spin ? spin->K2 : nullptr;
+  symmetrize_jk<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Jp, Kp, J, K, K2, K2, b->nbf);
   HF_CUDA(cudaGetLastError());
   if (nq) *nq = total;
   return HF_OK;
@@ -663,6 +700,47 @@ extern "C" int hf_fock_jk(hf_basis* b, const double* D, double* J, double* K, co
   } else {
     HF_CHECK(hf_fock_jk_device(b, D, J, K, o, nullptr));
   }
+  HF_CUDA(cudaStreamSynchronize(st));
+  return HF_OK;
+}
+
+__global__ void add_densities(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
+                              size_t nn) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t < nn) C[t] = A[t] + B[t];
+}
+
+int hf_fock_jk_uhf_device(hf_basis* b, const double* Da, const double* Db, const double* Dsum, double* J, double* Ka,
+                          double* Kb, const hf_jk_opts& o, long long* nq) {
+  hf_ctx* ctx = b->ctx;
+  cudaStream_t st = ctx->stream;
+  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound));
+  const size_t nn = (size_t)b->nbf * b->nbf;
+  HF_CUDA(cudaMemsetAsync(J, 0, nn * sizeof(double), st));
+  HF_CUDA(cudaMemsetAsync(Ka, 0, nn * sizeof(double), st));
+  HF_CUDA(cudaMemsetAsync(Kb, 0, nn * sizeof(double), st));
+  HF_CUDA(cudaMemsetAsync(b->counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
+  const JKSpin spin{Dsum, Db, Kb};
+  return hf_jk_run(b, Da, J, Ka, J, Ka, b->counters.ptr, o, st, nq, nullptr, &spin);
+}
+
+extern "C" int hf_fock_jk_uhf(hf_basis* b, const double* Da, const double* Db, double* J, double* Ka, double* Kb,
+                              const hf_jk_opts* opts) {
+  if (!b || !Da || !Db || !J || !Ka || !Kb) return hf_fail(HF_ERR_INVALID, "hf_fock_jk_uhf: null argument");
+  hf_jk_opts o;
+  hf_jk_opts_default(&o);
+  if (opts) o = *opts;
+  if (!(o.schwarz_tau >= 0.0) || !(o.fp32_bound >= 0.0)) return hf_fail(HF_ERR_INVALID, "negative threshold");
+  if (o.flags & HF_JK_HOST) return hf_fail(HF_ERR_INVALID, "hf_fock_jk_uhf: device pointers only");
+  hf_ctx* ctx = b->ctx;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  const size_t nn = (size_t)b->nbf * b->nbf;
+  if (b->Dsum.n != nn) HF_CHECK(b->Dsum.alloc(ctx, nn));
+  add_densities<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Da, Db, b->Dsum.ptr, nn);
+  HF_CUDA(cudaGetLastError());
+  HF_CHECK(hf_fock_jk_uhf_device(b, Da, Db, b->Dsum.ptr, J, Ka, Kb, o, nullptr));
   HF_CUDA(cudaStreamSynchronize(st));
   return HF_OK;
 }

@@ -25,6 +25,9 @@ extern "C" int hf_scf_solve_batch(hf_basis* const* bases, int count, const hf_sc
   hf_ctx* ctx = bases[0] ? bases[0]->ctx : nullptr;
   for (int i = 0; i < count; ++i)
     if (!bases[i] || bases[i]->ctx != ctx) return hf_fail(HF_ERR_INVALID, "basis %d missing or on another context", i);
+  for (int i = 0; i < count; ++i)
+    if (bases[i]->nelec % 2)
+      return hf_fail(HF_ERR_ODD_ELECTRONS, "basis %d: closed-shell RHF needs an even electron count", i);
   hf_scf_opts o;
   hf_scf_opts_default(&o);
   if (opts) o = *opts;

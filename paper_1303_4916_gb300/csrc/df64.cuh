@@ -73,6 +73,10 @@ __device__ __forceinline__ df64 df_fma(df64 a, df64 b, df64 c) {
   return df_quick_two_sum(s, err);
 }
 
+// a * b + c, the fused step the generated recurrences call for every
+// arithmetic type (FP64 and FP32 have theirs in the generated header)
+__device__ __forceinline__ df64 fmac(df64 a, df64 b, df64 c) { return df_fma(a, b, c); }
+
 // exact scaling by a power of two
 __device__ __forceinline__ df64 df_scale2(df64 a, float pow2) { return df64(a.hi * pow2, a.lo * pow2); }
 

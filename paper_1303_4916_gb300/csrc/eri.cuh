@@ -380,17 +380,23 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
     const PairSet P = mjp ? mjp->ps : ps;
     const int* ketb = mjp ? mjp->ketlist + mjp->ket_off[pair_class(C::LC, C::LD)] : w.ket;
     const int bp = __ldg(w.bra + bi);
-    const int kidx = __ldg(w.kbeg + bi) + 32 * (t - __ldg(w.ioff + bi)) + lane;
+    const int nsp = w.nsplit ? __ldg(w.nsplit + bi) : 1;
+    const int rr = t - __ldg(w.ioff + bi);
+    const int kblk = rr / nsp, part = rr - kblk * nsp;
+    const int kidx = __ldg(w.kbeg + bi) + 32 * kblk + lane;
     const bool active = kidx < __ldg(w.kend + bi);
     const int kp = active ? __ldg(ketb + kidx) : bp;
     const PairInfo bra = P.info[bp];
     const PairInfo ket = P.info[kp];
+    // this part's bra primitive pairs (all of them unless the item is split;
+    // the contraction is linear, so the parts' digested blocks add up)
+    const int ib0 = part * bra.nprim / nsp, ib1 = (part + 1) * bra.nprim / nsp;
 
     R acc[C::NE * C::NF];
     if constexpr (std::is_same<R, df64>::value)
-      contracted_vrr_df<C>(P, kc, bra.prim0, bra.nprim, ket.prim0, active ? ket.nprim : 0, acc);
+      contracted_vrr_df<C>(P, kc, bra.prim0 + ib0, ib1 - ib0, ket.prim0, active ? ket.nprim : 0, acc);
     else
-      contracted_vrr<C, R>(P, kc, bra.prim0, bra.nprim, ket.prim0, active ? ket.nprim : 0, acc);
+      contracted_vrr<C, R>(P, kc, bra.prim0 + ib0, ib1 - ib0, ket.prim0, active ? ket.nprim : 0, acc);
     R I[NA * NB * NC * ND];
     {
       R AB[3] = {(R)bra.AB[0], (R)bra.AB[1], (R)bra.AB[2]};
@@ -531,10 +537,10 @@ struct BoysSel<L, df64> {
   static __device__ __forceinline__ void eval(df64 T, const KernelCommon& kc, df64* F) { boys_df<L>(T, kc.boysdf, F); }
 };
 
-// a * b + c, fused in each arithmetic type of the cooperative kernel
+// a * b + c, fused in each arithmetic type of the cooperative kernel (the
+// df64 one sits beside df_fma, where argument-dependent lookup finds it)
 __device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ df64 fmac(df64 a, df64 b, df64 c) { return df_fma(a, b, c); }
 
 // Classes with L >= 5: one warp per contracted quartet.  The primitive
 // quartets are set up G at a time, one per lane: each lane forms its
@@ -598,14 +604,20 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
     const auto* pbase = mjp ? PrimBase<R>::get(mjp->ps) : base;
     const int* ketb = mjp ? mjp->ketlist + mjp->ket_off[pair_class(C::LC, C::LD)] : w.ket;
     const int bp = __ldg(w.bra + bi);
-    const int kp = __ldg(ketb + __ldg(w.kbeg + bi) + (t - __ldg(w.ioff + bi)));
+    const int nsp = w.nsplit ? __ldg(w.nsplit + bi) : 1;
+    const int rr = t - __ldg(w.ioff + bi);
+    const int kj = rr / nsp, part = rr - kj * nsp;
+    const int kp = __ldg(ketb + __ldg(w.kbeg + bi) + kj);
     const PairInfo bra = P.info[bp];
     const PairInfo ket = P.info[kp];
     R acc[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) acc[k] = (R)0;
-    const int nq = bra.nprim * ket.nprim;
-    for (int g0 = 0; g0 < nq; g0 += G) {
+    // this part's primitive quartets (all unless the item is split; the
+    // parts' digested blocks add up)
+    const int nq_all = bra.nprim * ket.nprim;
+    const int q_lo = part * nq_all / nsp, nq = (part + 1) * nq_all / nsp;
+    for (int g0 = q_lo; g0 < nq; g0 += G) {
       const int q = g0 + lane;
       if (lane < G && q < nq) {
         const int ib = q / ket.nprim, ik = q - ib * ket.nprim;
@@ -644,7 +656,7 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
         for (int m = 0; m <= C::L; ++m) cv[HF_NCOEF + m] = B[m] * pref;
       }
       __syncwarp();
-      const int ng = min(G, nq - g0);
+      const int ng = min(G, nq - g0);  // rows set up in this pass
       for (int jq = 0; jq < ng; ++jq) {
         const R* const cv = stage + jq * S::ROW;
         if (lane <= C::L) s[lane] = cv[HF_NCOEF + lane];
@@ -852,7 +864,12 @@ __global__ void __launch_bounds__(128) eri_store_kernel(const JKWork w, const Pa
     }
     const int bi = lo;
     const int bp = __ldg(w.bra + bi);
-    const int kidx = __ldg(w.kbeg + bi) + w.chunk * (t - __ldg(w.ioff + bi)) + lane;
+    // the tensor is written, not accumulated: part 0 of a split item takes
+    // the whole primitive loop and the other parts do nothing
+    const int nsp = w.nsplit ? __ldg(w.nsplit + bi) : 1;
+    const int rr = t - __ldg(w.ioff + bi);
+    if (rr % nsp != 0) continue;
+    const int kidx = __ldg(w.kbeg + bi) + w.chunk * (rr / nsp) + lane;
     if (lane >= w.chunk || kidx >= __ldg(w.kend + bi)) continue;
     const int kp = __ldg(w.ket + kidx);
     const PairInfo bra = ps.info[bp];

@@ -62,6 +62,22 @@ def coef(k, name):
     return name if k == 1 else f"((R){k} * {name})"
 
 
+def render(terms, init=None):
+    """Source of init + sum of terms as nested fused multiply-adds
+    fmac(a, b, c) = a*b + c (one FMA in FP64/FP32, one fused double-float
+    step in df64): c0*x0, then fmac(c1, x1, .), and c*(x2 - c3*x3) as
+    fmac(c, fmac(-c3, x3, x2), .)."""
+    def one(t, acc):
+        if t[0] == "p":
+            return f"{t[1]} * {t[2]}" if acc is None else f"fmac({t[1]}, {t[2]}, {acc})"
+        inner = f"fmac(-{t[3]}, {t[4]}, {t[2]})"
+        return f"{t[1]} * {inner}" if acc is None else f"fmac({t[1]}, {inner}, {acc})"
+    expr = init
+    for t in terms:
+        expr = one(t, expr)
+    return expr
+
+
 def pick_axis(v):
     # the axis with the largest power; ties broken towards x
     best = 0
@@ -105,6 +121,7 @@ class VRR:
             name = f"B[{m}]"
             self.memo[key] = name
             return name
+        # terms: ("p", c, x) is c*x; ("d", c, x2, c3, x3) is c*(x2 - c3*x3)
         terms = []
         # node spec: value = c0*x0 + c1*x1 + c2*(x2 - c3*x3) + c4*x4, inputs as
         # DAG keys (None = absent), coefficients as names in the coefficient vector
@@ -112,40 +129,40 @@ class VRR:
         if tl(f) > 0:
             i = pick_axis(f)
             f1 = add(f, i, -1)
-            terms.append(f"QC[{i}] * {self.get(e, f1, m)}")
-            terms.append(f"WQ[{i}] * {self.get(e, f1, m + 1)}")
+            terms.append(("p", f"QC[{i}]", self.get(e, f1, m)))
+            terms.append(("p", f"WQ[{i}]", self.get(e, f1, m + 1)))
             node["x"][0], node["c"][0] = (e, f1, m), f"QC{i}"
             node["x"][1], node["c"][1] = (e, f1, m + 1), f"WQ{i}"
             nflop = 3
             if f1[i] > 0:
                 f2 = add(f1, i, -1)
-                terms.append(f"{coef(f1[i], 'o2q')} * ({self.get(e, f2, m)} - rq * {self.get(e, f2, m + 1)})")
+                terms.append(("d", coef(f1[i], "o2q"), self.get(e, f2, m), "rq", self.get(e, f2, m + 1)))
                 node["x"][2], node["x"][3] = (e, f2, m), (e, f2, m + 1)
                 node["c"][2], node["c"][3] = f"o2q{f1[i]}", "rq"
                 nflop += 4 if f1[i] > 1 else 3
             if e[i] > 0:
                 e1 = add(e, i, -1)
-                terms.append(f"{coef(e[i], 'o2pq')} * {self.get(e1, f1, m + 1)}")
+                terms.append(("p", coef(e[i], "o2pq"), self.get(e1, f1, m + 1)))
                 node["x"][4], node["c"][4] = (e1, f1, m + 1), f"o2pq{e[i]}"
                 nflop += 3 if e[i] > 1 else 2
         else:
             i = pick_axis(e)
             e1 = add(e, i, -1)
-            terms.append(f"PA[{i}] * {self.get(e1, f, m)}")
-            terms.append(f"WP[{i}] * {self.get(e1, f, m + 1)}")
+            terms.append(("p", f"PA[{i}]", self.get(e1, f, m)))
+            terms.append(("p", f"WP[{i}]", self.get(e1, f, m + 1)))
             node["x"][0], node["c"][0] = (e1, f, m), f"PA{i}"
             node["x"][1], node["c"][1] = (e1, f, m + 1), f"WP{i}"
             nflop = 3
             if e1[i] > 0:
                 e2 = add(e1, i, -1)
-                terms.append(f"{coef(e1[i], 'o2p')} * ({self.get(e2, f, m)} - rp * {self.get(e2, f, m + 1)})")
+                terms.append(("d", coef(e1[i], "o2p"), self.get(e2, f, m), "rp", self.get(e2, f, m + 1)))
                 node["x"][2], node["x"][3] = (e2, f, m), (e2, f, m + 1)
                 node["c"][2], node["c"][3] = f"o2p{e1[i]}", "rp"
                 nflop += 4 if e1[i] > 1 else 3
         name = f"v{self.nvar}"
         self.nvar += 1
-        self.lines.append(f"const R {name} = {' + '.join(terms)};")
-        self.exprs[name] = " + ".join(terms)
+        self.lines.append(f"const R {name} = {render(terms)};")
+        self.exprs[name] = terms
         self.flops += nflop
         self.memo[key] = name
         self.nodes.append((name, key, node))
@@ -157,7 +174,7 @@ class VRR:
             for ei, e in enumerate(self.E.comps):
                 targets.append((ei * len(self.F) + fi, self.get(e, f, 0)))
         # a target no other node reads is folded into its accumulation:
-        # acc = acc + t0 + t1 + ..., which contracts into FMAs
+        # acc = fmac(c1, x1, fmac(c0, x0, acc)), one fused step per term
         used = set()
         for name, key, node in self.nodes:
             for x in node["x"]:
@@ -168,7 +185,7 @@ class VRR:
         acc_lines = []
         for k, v in targets:
             if v in folded:
-                acc_lines.append(f"acc[{k}] = acc[{k}] + {self.exprs[v]};")
+                acc_lines.append(f"acc[{k}] = {render(self.exprs[v], f'acc[{k}]')};")
             else:
                 acc_lines.append(f"acc[{k}] += {v};")
         self.flops += len(acc_lines)
@@ -331,6 +348,11 @@ def emit(lmax):
     o.append(f"#define HF_GEN_NCLASS {len(cls)}")
     o.append("")
     o.append("namespace hfgen {")
+    o.append("")
+    o.append("// a * b + c, fused, for the built-in arithmetic types; the double-float type")
+    o.append("// brings its own fmac, found by argument-dependent lookup")
+    o.append("__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }")
+    o.append("__device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }")
     o.append("")
     table = []
     coop_tables = []

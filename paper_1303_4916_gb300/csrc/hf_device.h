@@ -95,8 +95,12 @@ struct JKWork {
   const int* ket;   // ket list of the ket class (single-molecule launches)
   const int* kbeg;  // [nbra] first ket index of each entry
   const int* kend;  // [nbra] one past the last ket index
-  const int* ioff;  // [nbra+1] first work item of each entry (32 kets per item)
+  const int* ioff;  // [nbra+1] first work item of each entry (32 kets per item, times nsplit)
   const int* mol;   // [nbra] molecule of each entry (multi-molecule launches), else null
+  const int* nsplit;  // [nbra] parts each item of the entry is split into along its primitive
+                      // loop (bra primitive pairs, or primitive quartets for warp-cooperative
+                      // classes); null = 1.  Item t of entry e is ket block (t - ioff[e]) / nsplit[e],
+                      // part (t - ioff[e]) % nsplit[e].
   int nbra;
   int nitems;
   int* counter;     // work-item counter, zero before the launch

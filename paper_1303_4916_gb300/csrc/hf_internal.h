@@ -79,8 +79,8 @@ struct DevArray {
 
 // ------------------------------------------------------------- basis
 struct ClassWork {
-  DevArray<int> bra, kbeg, kend, ioff;
-  std::vector<int> bra_h, kbeg_h, kend_h;  // host copies (multi-molecule launches, statistics)
+  DevArray<int> bra, kbeg, kend, ioff, nsplit;
+  std::vector<int> bra_h, kbeg_h, kend_h, nsplit_h;  // host copies (multi-molecule launches, statistics)
   JKWork w{};
   long long nquartets = 0;
 };
@@ -116,6 +116,8 @@ struct hf_basis {
 
   // scratch used by host-pointer J/K calls
   DevArray<double> hD, hJ, hK;
+  // D^a + D^b of an unrestricted J/K call
+  DevArray<double> Dsum;
 
   // one-electron data (lazily)
   DevArray<double> S, T, V;
@@ -148,12 +150,11 @@ int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const 
 // Grid of a persistent class launch: enough blocks of 4 warps for the work
 // items, at most occ resident blocks on every SM.
 int hf_launch_grid(hf_ctx* ctx, int occ, int nitems);
-// Shape of a class launch of nitems work items, occ resident 4-warp blocks
-// per SM (at most cap_per_sm when cap_per_sm > 0).  A class with at least
-// as many items as resident warps runs persistent 4-warp blocks that pull
-// items from the counter; a smaller one runs one-warp blocks, one per item,
-// so the few items (each a long serial primitive loop) spread over all SMs
-// instead of filling the four warps of the first few blocks.
+// Shape of a class launch of nitems work items: persistent 4-warp blocks
+// that pull items from the counter, enough for the items and at most occ
+// (or cap_per_sm when cap_per_sm > 0) resident blocks on every SM.  (One-warp
+// blocks for classes with few items were measured on GB300 and did not
+// shorten them: a small class is bound by its longest item.)
 struct LaunchShape {
   int grid, threads;
 };
@@ -169,8 +170,16 @@ struct JKClassTiming {
 // with the work-item counters at counters[0 .. 2*HF_NCLASS) (zeroed by the
 // caller), then writes J = 2 (Jp + Jp^T), K = Kp + Kp^T (J == Jp and K == Kp
 // for in place).  df64 and FP32 tiers as o.flags says.
+// Second spin of an unrestricted build: J from Dj (D^a + D^b), and K2
+// (zeroed by the caller, symmetrised in place) from D2.
+struct JKSpin {
+  const double* Dj;
+  const double* D2;
+  double* K2;
+};
 int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, double* K, int* counters,
-              const hf_jk_opts& o, cudaStream_t st, long long* nquartets, JKClassTiming* timing);
+              const hf_jk_opts& o, cudaStream_t st, long long* nquartets, JKClassTiming* timing,
+              const JKSpin* spin = nullptr);
 int hf_boys_tables(hf_ctx* ctx);
 int hf_eri_tensor_device(hf_basis* b, double* G);
 int hf_jk_stored_device(hf_basis* b, const double* G, const double* D, double* J, double* K);

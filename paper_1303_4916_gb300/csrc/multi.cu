@@ -67,22 +67,25 @@ int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vec
   if (nmol > 0)
     HF_CUDA(cudaMemcpyAsync(table.ptr, table_h.data(), sizeof(MolJK) * nmol, cudaMemcpyHostToDevice, st));
   HF_CHECK(counters.alloc(ctx, 2 * HF_NCLASS));
-  std::vector<int> hb, hkb, hke, hio, hm;
+  std::vector<int> hb, hkb, hke, hio, hm, hs;
   for (int c2 = 0; c2 < 2 * HF_NCLASS; ++c2) {
     const int cls = c2 / 2, r = c2 % 2;
-    hb.clear(); hkb.clear(); hke.clear(); hm.clear(); hio.assign(1, 0);
+    hb.clear(); hkb.clear(); hke.clear(); hm.clear(); hs.clear(); hio.assign(1, 0);
     long long nq = 0;
     for (int m = 0; m < nmol; ++m) {
       const ClassWork& cw = r == 0 ? mols[m]->work64[cls] : mols[m]->work32[cls];
       for (size_t e = 0; e < cw.bra_h.size(); ++e) {
         const int cnt = cw.kend_h[e] - cw.kbeg_h[e];
+        const int nsp = cw.nsplit_h.empty() ? 1 : cw.nsplit_h[e];
         // item offsets are int on the device: checked in 64 bits per entry
-        const long long next = (long long)hio.back() + (cnt + ctx->ops[cls].chunk - 1) / ctx->ops[cls].chunk;
+        const long long next =
+            (long long)hio.back() + (long long)((cnt + ctx->ops[cls].chunk - 1) / ctx->ops[cls].chunk) * nsp;
         if (next > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "batched class %d: too many work items", cls);
         hb.push_back(cw.bra_h[e]);
         hkb.push_back(cw.kbeg_h[e]);
         hke.push_back(cw.kend_h[e]);
         hm.push_back(m);
+        hs.push_back(nsp);
         hio.push_back((int)next);
         nq += cnt;
         mol_quartets[m] += cnt;
@@ -94,7 +97,9 @@ int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vec
     HF_CHECK(kend[c2].alloc(ctx, nb));
     HF_CHECK(mol[c2].alloc(ctx, nb));
     HF_CHECK(ioff[c2].alloc(ctx, nb + 1));
+    HF_CHECK(nsplit[c2].alloc(ctx, nb));
     if (nb > 0) {
+      HF_CUDA(cudaMemcpyAsync(nsplit[c2].ptr, hs.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
       HF_CUDA(cudaMemcpyAsync(bra[c2].ptr, hb.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
       HF_CUDA(cudaMemcpyAsync(kbeg[c2].ptr, hkb.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
       HF_CUDA(cudaMemcpyAsync(kend[c2].ptr, hke.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
@@ -108,6 +113,7 @@ int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vec
     wk.kend = kend[c2].ptr;
     wk.ioff = ioff[c2].ptr;
     wk.mol = mol[c2].ptr;
+    wk.nsplit = nsplit[c2].ptr;
     wk.nbra = nb;
     wk.nitems = hio.back();
     wk.counter = counters.ptr + c2;
@@ -116,6 +122,16 @@ int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vec
     // the host vectors are reused for the next class: let the copies finish
     HF_CUDA(cudaStreamSynchronize(st));
   }
+  return HF_OK;
+}
+
+int MultiJK::set_spin(int m, const double* Dj, const double* D2, double* K2) {
+  if (m < 0 || m >= nmol) return hf_fail(HF_ERR_INVALID, "set_spin: molecule %d", m);
+  table_h[m].Dj = Dj;
+  table_h[m].D2 = D2;
+  table_h[m].K2 = K2;
+  HF_CUDA(cudaMemcpyAsync(table.ptr, table_h.data(), sizeof(MolJK) * nmol, cudaMemcpyHostToDevice, ctx->stream));
+  HF_CUDA(cudaStreamSynchronize(ctx->stream));
   return HF_OK;
 }
 

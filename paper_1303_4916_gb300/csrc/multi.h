@@ -14,7 +14,7 @@ struct MultiJK {
   std::vector<MolJK> table_h;
   DevArray<MolJK> table;
   DevArray<int> bra[2 * HF_NCLASS], kbeg[2 * HF_NCLASS], kend[2 * HF_NCLASS], ioff[2 * HF_NCLASS],
-      mol[2 * HF_NCLASS];
+      mol[2 * HF_NCLASS], nsplit[2 * HF_NCLASS];
   JKWork w[2 * HF_NCLASS] = {};
   long long nquartets[2 * HF_NCLASS] = {};
   std::vector<long long> mol_quartets;  // per molecule, all classes
@@ -28,6 +28,9 @@ struct MultiJK {
             const std::vector<double*>& J, const std::vector<double*>& K);
   // Mark molecules active/inactive (uploads the table).
   int set_active(const std::vector<int>& active);
+  // Make molecule m's build unrestricted: J from Dj (D^a + D^b), K from its
+  // D (alpha) and K2 from D2 (beta) in the same launch (uploads the table).
+  int set_spin(int m, const double* Dj, const double* D2, double* K2);
   // Zero J/K of active molecules, run all classes, symmetrise.  With
   // class_ms, each class launch is bracketed by events and its duration in
   // ms is added to class_ms[cls] (the caller synchronises).

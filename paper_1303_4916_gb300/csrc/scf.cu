@@ -26,10 +26,11 @@
 
 namespace {
 
+// F = H + jf J - K  (jf = 2 closed shell, 1 per spin of an unrestricted build)
 __global__ void k_add_fock(const double* __restrict__ H, const double* __restrict__ J, const double* __restrict__ K,
-                           double* __restrict__ F, size_t nn) {
+                           double* __restrict__ F, size_t nn, double jf = 2.0) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t < nn) F[t] = H[t] + 2.0 * J[t] - K[t];
+  if (t < nn) F[t] = H[t] + jf * J[t] - K[t];
 }
 
 __global__ void k_add(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C, size_t nn) {
@@ -308,15 +309,13 @@ int scf_post_jk(hf_basis* b, ScfState& s) {
   return HF_OK;
 }
 
-// Phase 3 (after the stream has passed phase 2): energy and DIIS
-// bookkeeping on the host, then enqueue the next F (extrapolated or F_k).
-int scf_diis_step(hf_basis* b, ScfState& s) {
+// DIIS on the host from the dot products in s.hscal, then enqueue the next
+// F (extrapolated, or F_k) into Fout; vectors of len doubles (n^2, or 2 n^2
+// for the stacked spins of an unrestricted SCF) in the rings.
+static int diis_extrapolate(hf_basis* b, ScfState& s, size_t nn, double* Fout, const double* Fk) {
   hf_ctx* ctx = b->ctx;
   cudaStream_t st = ctx->stream;
-  const size_t nn = (size_t)s.n * s.n;
   const double* sc = s.hscal;
-  s.energy = sc[0] + b->e_nuc;
-  s.diis_error = sc[1];  // bit pattern of a non-negative double: ordering preserved by atomicMax
   if (s.m > 0) {
     const int k = (int)s.slots.size();
     for (int i = 0; i < k; ++i)
@@ -348,13 +347,22 @@ int scf_diis_step(hf_basis* b, ScfState& s) {
       const int mm = k - first;
       for (int i = 0; i < mm; ++i) s.hcoef[i] = c[i];
       HF_CUDA(cudaMemcpyAsync(s.scal.ptr + 20, s.hcoef, sizeof(double) * mm, cudaMemcpyHostToDevice, st));
-      k_lincomb<<<blocks(nn), 256, 0, st>>>(s.Fring.ptr, s.islots.ptr + first, s.scal.ptr + 20, mm, nn, s.F.ptr);
+      k_lincomb<<<blocks(nn), 256, 0, st>>>(s.Fring.ptr, s.islots.ptr + first, s.scal.ptr + 20, mm, nn, Fout);
       HF_CUDA(cudaGetLastError());
       return HF_OK;
     }
   }
-  HF_CUDA(cudaMemcpyAsync(s.F.ptr, s.Fk.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  HF_CUDA(cudaMemcpyAsync(Fout, Fk, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
   return HF_OK;
+}
+
+// Phase 3 (after the stream has passed phase 2): energy and DIIS
+// bookkeeping on the host, then enqueue the next F (extrapolated or F_k).
+int scf_diis_step(hf_basis* b, ScfState& s) {
+  const double* sc = s.hscal;
+  s.energy = sc[0] + b->e_nuc;
+  s.diis_error = sc[1];  // bit pattern of a non-negative double: ordering preserved by atomicMax
+  return diis_extrapolate(b, s, (size_t)s.n * s.n, s.F.ptr, s.Fk.ptr);
 }
 
 // One full iteration for a single molecule.
@@ -450,6 +458,8 @@ bool scf_after_iter(hf_basis* b, ScfState& s, const hf_scf_opts& o) {
 
 extern "C" int hf_scf_solve(hf_basis* b, const hf_scf_opts* opts, hf_scf_result* res) {
   if (!b || !res) return hf_fail(HF_ERR_INVALID, "hf_scf_solve: null argument");
+  if (b->nelec % 2)
+    return hf_fail(HF_ERR_ODD_ELECTRONS, "closed-shell RHF needs an even electron count (%d)", b->nelec);
   hf_scf_opts o;
   hf_scf_opts_default(&o);
   if (opts) o = *opts;
@@ -493,4 +503,202 @@ extern "C" int hf_scf_solve(hf_basis* b, const hf_scf_opts* opts, hf_scf_result*
   HF_CHECK(scf_finish(b, s, res));
   res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return s.converged ? HF_OK : hf_fail(HF_ERR_NOT_CONVERGED, "SCF not converged in %d iterations", s.iter);
+}
+
+// ------------------------------------------------------------- unrestricted HF
+// Pople-Nesbet equations as Szabo-Ostlund state them (the paper's test
+// calculations are UHF): per spin s with n_s electrons, D^s = C^s_occ
+// C^s_occ^T, F^s = H + J[D^a + D^b] - K[D^s], E = (1/2) sum_s Tr[D^s (H +
+// F^s)] + E_nuc; core guess F^a = F^b = H; with DIIS the two errors
+// e^s = F^s D^s S - S D^s F^s are one stacked vector with one set of
+// coefficients for both spins.  J, K^a and K^b come from one evaluation of
+// the integrals per iteration (the J/K phase replayed from a CUDA graph).
+// Buffers hold the two spins back to back: X2[0..n^2) alpha, [n^2..2n^2) beta.
+namespace {
+
+struct UhfState {
+  ScfState s;  // shared: H, X, W, T1, T2, J, syevd workspace, scalars, DIIS rings (2 n^2 per slot)
+  DevArray<double> F2, Fk2, C2, D2, K2, eps2, Dsum;
+};
+
+int uhf_init(hf_basis* b, UhfState& u, int diis_size) {
+  hf_ctx* ctx = b->ctx;
+  HF_CHECK(scf_state_init(b, u.s, 0));
+  const size_t nn = (size_t)b->nbf * b->nbf;
+  u.s.m = std::max(0, std::min(diis_size, 16));
+  if (u.s.m > 0) {
+    HF_CHECK(u.s.Fring.alloc(ctx, 2 * nn * u.s.m));
+    HF_CHECK(u.s.Ering.alloc(ctx, 2 * nn * u.s.m));
+  }
+  HF_CHECK(u.F2.alloc(ctx, 2 * nn));
+  HF_CHECK(u.Fk2.alloc(ctx, 2 * nn));
+  HF_CHECK(u.C2.alloc(ctx, 2 * nn));
+  HF_CHECK(u.D2.alloc(ctx, 2 * nn));
+  HF_CHECK(u.K2.alloc(ctx, 2 * nn));
+  HF_CHECK(u.eps2.alloc(ctx, 2 * (size_t)b->nbf));
+  HF_CHECK(u.Dsum.alloc(ctx, nn));
+  return HF_OK;
+}
+
+// F'^s = X F^s X, eigenvectors, C^s = X C'^s, D^s = C^s_occ C^s_occ^T, D^a + D^b.
+int uhf_density(hf_basis* b, UhfState& u, const int nocc[2]) {
+  hf_ctx* ctx = b->ctx;
+  cudaStream_t st = ctx->stream;
+  ScfState& s = u.s;
+  const int n = s.n;
+  const size_t nn = (size_t)n * n;
+  for (int sp = 0; sp < 2; ++sp) {
+    double* F = u.F2.ptr + sp * nn;
+    double* Cm = u.C2.ptr + sp * nn;
+    double* Dm = u.D2.ptr + sp * nn;
+    HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, F, n, s.X.ptr, n, s.T1.ptr, n));
+    HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, s.X.ptr, n, s.T1.ptr, n, s.W.ptr, n));
+    HF_CHECK(syevd(ctx, s, s.W.ptr, u.eps2.ptr + (size_t)sp * n));
+    HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, s.X.ptr, n, s.W.ptr, n, Cm, n));
+    if (nocc[sp] > 0) HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_T, n, n, nocc[sp], Cm, n, Cm, n, Dm, n));
+    else HF_CUDA(cudaMemsetAsync(Dm, 0, nn * sizeof(double), st));
+  }
+  k_add<<<blocks(nn), 256, 0, st>>>(u.D2.ptr, u.D2.ptr + nn, u.Dsum.ptr, nn);
+  HF_CUDA(cudaGetLastError());
+  return HF_OK;
+}
+
+// F^s = H + J - K^s, E (both spins into scal[0]), stacked DIIS error, dots.
+int uhf_post_jk(hf_basis* b, UhfState& u) {
+  hf_ctx* ctx = b->ctx;
+  cudaStream_t st = ctx->stream;
+  ScfState& s = u.s;
+  const int n = s.n;
+  const size_t nn = (size_t)n * n;
+  s.fock_builds += 1;
+  HF_CUDA(cudaMemsetAsync(s.scal.ptr, 0, sizeof(double) * 40, st));
+  double* err = s.m > 0 ? s.Ering.ptr + (size_t)s.next * 2 * nn : nullptr;
+  for (int sp = 0; sp < 2; ++sp) {
+    double* Fk = u.Fk2.ptr + sp * nn;
+    const double* Dm = u.D2.ptr + sp * nn;
+    k_add_fock<<<blocks(nn), 256, 0, st>>>(s.H.ptr, s.J.ptr, u.K2.ptr + sp * nn, Fk, nn, 1.0);
+    k_energy<<<std::min(blocks(nn), 1024u), 256, 0, st>>>(Dm, s.H.ptr, Fk, nn, s.scal.ptr);
+    HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, Dm, n, b->S.ptr, n, s.T1.ptr, n));
+    HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, Fk, n, s.T1.ptr, n, s.T2.ptr, n));
+    k_antisym<<<blocks(nn), 256, 0, st>>>(s.T2.ptr, err ? err + sp * nn : s.T1.ptr, n,
+                                          (unsigned long long*)(s.scal.ptr + 1));
+  }
+  if (s.m > 0) {
+    HF_CUDA(cudaMemcpyAsync(s.Fring.ptr + (size_t)s.next * 2 * nn, u.Fk2.ptr, 2 * nn * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st));
+    s.slots.push_back(s.next);
+    if ((int)s.slots.size() > s.m) s.slots.erase(s.slots.begin());
+    s.next = (s.next + 1) % s.m;
+    const int k = (int)s.slots.size();
+    for (int i = 0; i < k; ++i) s.hslots[i] = s.slots[i];
+    HF_CUDA(cudaMemcpyAsync(s.islots.ptr, s.hslots, sizeof(int) * k, cudaMemcpyHostToDevice, st));
+    k_multi_dot<<<dim3(std::min(blocks(2 * nn), 64u), k), 256, 0, st>>>(s.Ering.ptr, s.islots.ptr, k, err, 2 * nn,
+                                                                        s.scal.ptr + 2);
+  }
+  HF_CUDA(cudaGetLastError());
+  HF_CUDA(cudaMemcpyAsync(s.hscal, s.scal.ptr, sizeof(double) * 18, cudaMemcpyDeviceToHost, st));
+  return HF_OK;
+}
+
+// <S^2> = S_z (S_z + 1) + n_b - sum_ij (C^a_occ^T S C^b_occ)_ij^2
+int uhf_s2(hf_basis* b, UhfState& u, const int nocc[2], double* s2) {
+  hf_ctx* ctx = b->ctx;
+  ScfState& s = u.s;
+  const int n = s.n;
+  const size_t nn = (size_t)n * n;
+  const double sz = 0.5 * (nocc[0] - nocc[1]);
+  double ov2 = 0.0;
+  if (nocc[0] > 0 && nocc[1] > 0) {
+    HF_CHECK(gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, n, nocc[1], n, b->S.ptr, n, u.C2.ptr + nn, n, s.T1.ptr, n));
+    HF_CHECK(gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, nocc[0], nocc[1], n, u.C2.ptr, n, s.T1.ptr, n, s.T2.ptr, nocc[0]));
+    double nrm = 0.0;
+    cublasPointerMode_t pm;
+    cublasGetPointerMode(ctx->cublas, &pm);
+    cublasSetPointerMode(ctx->cublas, CUBLAS_POINTER_MODE_HOST);
+    const cublasStatus_t cs = cublasDnrm2(ctx->cublas, nocc[0] * nocc[1], s.T2.ptr, 1, &nrm);
+    cublasSetPointerMode(ctx->cublas, pm);
+    if (cs != CUBLAS_STATUS_SUCCESS) return hf_fail(HF_ERR_CUDA, "cublasDnrm2 failed");
+    ov2 = nrm * nrm;
+  }
+  *s2 = sz * (sz + 1.0) + nocc[1] - ov2;
+  return HF_OK;
+}
+
+}  // namespace
+
+extern "C" int hf_uhf_solve(hf_basis* b, int n_alpha, int n_beta, const hf_scf_opts* opts, hf_uhf_result* res) {
+  if (!b || !res) return hf_fail(HF_ERR_INVALID, "hf_uhf_solve: null argument");
+  if (n_beta < 0 || n_alpha < n_beta || n_alpha > b->nbf)
+    return hf_fail(HF_ERR_INVALID, "hf_uhf_solve: need nbf >= n_alpha >= n_beta >= 0 (%d, %d)", n_alpha, n_beta);
+  hf_scf_opts o;
+  hf_scf_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.max_iter < 1 || o.diis_size < 0 || !(o.e_tol >= 0.0) || (o.flags & HF_SCF_STORED_ERI) || o.D0 ||
+      (o.jk.flags & HF_JK_HOST))
+    return hf_fail(HF_ERR_INVALID, "hf_uhf_solve: bad options (direct J/K, core guess, device buffers)");
+  if (!(o.jk.schwarz_tau >= 0.0) || !(o.jk.fp32_bound >= 0.0)) return hf_fail(HF_ERR_INVALID, "negative threshold");
+  hf_ctx* ctx = b->ctx;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  const int nocc[2] = {n_alpha, n_beta};
+  const size_t nn = (size_t)b->nbf * b->nbf;
+  UhfState u;
+  ScfState& s = u.s;
+  HF_CHECK(uhf_init(b, u, o.diis_size));
+  HF_CHECK(scf_setup(b, s));
+  HF_CUDA(cudaMemcpyAsync(u.F2.ptr, s.H.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  HF_CUDA(cudaMemcpyAsync(u.F2.ptr + nn, s.H.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  HF_CHECK(hf_basis_prepare_work(b, o.jk.schwarz_tau, o.jk.fp32_bound));
+  MultiJK mj;
+  mj.jk_flags = o.jk.flags;
+  const KernelCommon kc = hf_kernel_common(ctx, o.jk.flags);
+  HF_CHECK(mj.build(ctx, {b}, {u.D2.ptr}, {s.J.ptr}, {u.K2.ptr}));
+  HF_CHECK(mj.set_spin(0, u.Dsum.ptr, u.D2.ptr + nn, u.K2.ptr + nn));
+  HF_CHECK(mj.capture(kc));
+  s.iter = 0;
+  s.e_old = NAN;
+  s.delta_e = NAN;
+  for (;;) {
+    HF_CHECK(uhf_density(b, u, nocc));
+    HF_CHECK(mj.run(kc));
+    s.quartets += mj.mol_quartets[0];
+    HF_CHECK(uhf_post_jk(b, u));
+    HF_CUDA(cudaStreamSynchronize(st));
+    s.energy = 0.5 * s.hscal[0] + b->e_nuc;
+    s.diis_error = s.hscal[1];
+    HF_CHECK(diis_extrapolate(b, s, 2 * nn, u.F2.ptr, u.Fk2.ptr));
+    s.iter += 1;
+    bool done = false;
+    if (!std::isnan(s.e_old)) {
+      s.delta_e = fabs(s.energy - s.e_old);
+      if (s.delta_e <= o.e_tol) {
+        s.converged = 1;
+        done = true;
+      }
+    }
+    s.e_old = s.energy;
+    if (done || s.iter >= o.max_iter) break;
+  }
+  double s2 = 0.0;
+  HF_CHECK(uhf_s2(b, u, nocc, &s2));
+  res->energy = s.energy;
+  res->e_nuc = b->e_nuc;
+  res->e_elec = s.energy - b->e_nuc;
+  res->delta_e = s.delta_e;
+  res->diis_error = s.diis_error;
+  res->s2 = s2;
+  res->iterations = s.iter;
+  res->converged = s.converged;
+  res->fock_builds = s.fock_builds;
+  res->quartets = s.quartets;
+  if (res->Da) HF_CUDA(cudaMemcpyAsync(res->Da, u.D2.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (res->Db) HF_CUDA(cudaMemcpyAsync(res->Db, u.D2.ptr + nn, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (res->eps_a) HF_CUDA(cudaMemcpyAsync(res->eps_a, u.eps2.ptr, sizeof(double) * b->nbf, cudaMemcpyDeviceToDevice, st));
+  if (res->eps_b)
+    HF_CUDA(cudaMemcpyAsync(res->eps_b, u.eps2.ptr + b->nbf, sizeof(double) * b->nbf, cudaMemcpyDeviceToDevice, st));
+  HF_CUDA(cudaStreamSynchronize(st));
+  res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return s.converged ? HF_OK : hf_fail(HF_ERR_NOT_CONVERGED, "UHF not converged in %d iterations", s.iter);
 }

@@ -3,8 +3,11 @@
 // paper_1303_4916_gb300/csrc/eri_classes.cuh, compiled for the CPU with the
 // device qualifiers defined away, behind plain C entry points that
 // tests/test_codegen_host.py calls through ctypes.
+#include <cmath>
 #define __device__
 #define __forceinline__ inline
+using std::fma;
+using std::fmaf;
 #include "eri_classes.cuh"
 
 // q = PA[3] WP[3] QC[3] WQ[3] o2p o2q o2pq rp rq

@@ -262,8 +262,9 @@ def test_df64_full_size_and_scf(ctx, hf):
 
 def test_errors(ctx, hf):
     mol = lattice_molecule(3, 1, "sp")
+    odd = hf.Basis(ctx, mol, n_electrons=3)      # a basis takes any count; closed-shell RHF does not
     with pytest.raises(hf.HFError) as e:
-        hf.Basis(ctx, mol, n_electrons=3)
+        odd.scf()
     assert e.value.code == -8
     bad = mol.copy()
     bad.shell_l = bad.shell_l.copy()
