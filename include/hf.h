@@ -88,7 +88,13 @@ typedef struct {
 
 /* J/K build options.  hf_jk_opts_default() fills the defaults shown. */
 #define HF_JK_HOST 1u              /* D, J, K are host pointers: copies are done inside the call */
-#define HF_JK_DETERMINISTIC 2u     /* reserved: accepted, currently same as default order */
+#define HF_JK_DETERMINISTIC 2u     /* bitwise reproducible J, K: contributions accumulate as
+                                      fixed-point integers (units 2^-20 and 2^-56 per
+                                      element, order-independent) instead of FP64 atomics;
+                                      hf_fock_jk, hf_fock_jk_profiled and hf_fock_jk_uhf
+                                      only (the basis keeps 32 bytes of device scratch per
+                                      matrix element, 48 for hf_fock_jk_uhf); the SCF,
+                                      batch, serving and no-alloc calls reject it */
 #define HF_JK_FP32_BOYS 4u         /* reduced-precision quartets also evaluate F_m(T) in FP32 */
 #define HF_JK_DF64 8u              /* quartets above fp32_bound run in double-float (FP32-pair)
                                       arithmetic, ~1e-14 relative, in every class (J/K
@@ -144,11 +150,30 @@ const char* hf_last_error(void);
  * creates its own stream, ordered after the legacy default stream).  Errors: HF_ERR_INVALID,
  * HF_ERR_CUDA (no device), HF_ERR_OOM. */
 int hf_ctx_create(hf_ctx** out, int device, size_t hbm_budget, void* cuda_stream);
+/* Destroy a context.  Bases and servers created on it and not yet
+ * destroyed keep it alive: the last hf_basis_destroy or hf_serve_destroy
+ * completes the teardown (no new basis may be created on it meanwhile:
+ * HF_ERR_INVALID). */
 void hf_ctx_destroy(hf_ctx* ctx);
 /* The stream all work of this context is ordered on (a cudaStream_t). */
 void* hf_ctx_stream(hf_ctx* ctx);
 /* Number of SMs of the context's device. */
 int hf_ctx_num_sms(hf_ctx* ctx);
+
+/* Log every SCF iteration of this context (hf_scf_solve, hf_uhf_solve,
+ * hf_scf_solve_batch, serving) as one JSON line appended to the file
+ * `path` ("-" = stderr, NULL = logging off, the default):
+ *   {"event": "scf_iter", "solver": "rhf"|"uhf"|"batch"|"serve", "mol": tag,
+ *    "nbf": n, "iter": k, "energy": E_k, "delta_e": |E_k - E_{k-1}| or null,
+ *    "diis_error": max |F D S - S D F|, "t": seconds since the solve began,
+ *    "converged": 0|1}
+ * Errors: HF_ERR_INVALID (null context, file cannot be opened). */
+int hf_ctx_set_log(hf_ctx* ctx, const char* path);
+
+/* 1 when the library was built with -DHF_BOUNDS_CHECK (every index of the
+ * J/K kernels checked before use, a failure returned as HF_ERR_INVALID
+ * naming the index; for small test cases), else 0. */
+int hf_bounds_checked(void);
 
 /* Fault-injection hook for tests: make the n-th device allocation from now
  * on fail with HF_ERR_OOM (n >= 1); n = 0 disables.  Host-side only. */
@@ -304,6 +329,22 @@ typedef struct {
  * HF_SCF_STORED_ERI and D0 (HF_ERR_INVALID).  Returns HF_ERR_NOT_CONVERGED
  * (result filled) after max_iter, HF_ERR_LINDEP as hf_scf_solve. */
 int hf_uhf_solve(hf_basis* b, int n_alpha, int n_beta, const hf_scf_opts* opts, hf_uhf_result* res);
+
+/* ---------------------------------------------------------------- MP2 */
+
+/* Second-order Moller-Plesset correlation energy of a closed-shell RHF
+ * solution, the paper's MP2 (Sec. "Capabilities"; its MP2 follows
+ * Szabo-Ostlund):
+ *   E(2) = sum_{i,j occ} sum_{a,b virt} (ia|jb) [2 (ia|jb) - (ib|ja)]
+ *                                        / (e_i + e_j - e_a - e_b)
+ * over the canonical orbitals, (ia|jb) from the stored AO tensor of Eq. 5
+ * by four one-index transformations (small bases: nbf <= 128; the call
+ * allocates nbf^4 + nbf^3 n_occ doubles of device memory while it runs).
+ * C: nbf x nbf DEVICE, row-major, C[mu][p] = coefficient of AO mu in MO p
+ * (as hf_scf_result.C); eps: nbf orbital energies, ascending, DEVICE;
+ * n_occ in [1, nbf).  *e2 (host) receives E(2).  Errors: HF_ERR_INVALID,
+ * HF_ERR_OOM, HF_ERR_CUDA. */
+int hf_mp2_energy(hf_basis* b, const double* C, const double* eps, int n_occ, double* e2);
 
 /* ---------------------------------------------------------------- batch */
 

@@ -17,6 +17,7 @@ from .api import (  # noqa: F401
     hf_fock_jk_uhf,
     hf_fock_jk_noalloc,
     hf_jk_stored,
+    hf_mp2_energy,
     hf_one_electron,
     hf_scf_solve,
     hf_scf_solve_batch,

@@ -9,7 +9,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhf.so")
+# HF_LIB selects another build of the same ABI, e.g. the bounds-checked
+# libhf_bcheck.so (paper_1303_4916_gb300.build.build_bounds_checked())
+LIB_PATH = os.environ.get("HF_LIB") or os.path.join(HERE, "libhf.so")
 
 HF_OK = 0
 HF_PENDING = 1
@@ -113,6 +115,8 @@ SIGNATURES = {
     "hf_ctx_stream": (P, [P]),
     "hf_ctx_num_sms": (I, [P]),
     "hf_ctx_inject_alloc_failure": (None, [P, I]),
+    "hf_ctx_set_log": (I, [P, C.c_char_p]),
+    "hf_bounds_checked": (I, []),
     "hf_basis_create": (I, [P, C.POINTER(hf_atom), I, C.POINTER(hf_shell), I, P, P, I, C.POINTER(P)]),
     "hf_basis_destroy": (None, [P]),
     "hf_basis_nbf": (I, [P]),
@@ -130,6 +134,7 @@ SIGNATURES = {
     "hf_scf_solve": (I, [P, C.POINTER(hf_scf_opts), C.POINTER(hf_scf_result)]),
     "hf_fock_jk_uhf": (I, [P, P, P, P, P, P, C.POINTER(hf_jk_opts)]),
     "hf_uhf_solve": (I, [P, I, I, C.POINTER(hf_scf_opts), C.POINTER(hf_uhf_result)]),
+    "hf_mp2_energy": (I, [P, P, P, I, C.POINTER(D)]),
     "hf_scf_solve_batch": (I, [C.POINTER(P), I, C.POINTER(hf_scf_opts), C.POINTER(hf_scf_result),
                                C.POINTER(I)]),
     "hf_serve_opts_default": (None, [C.POINTER(hf_serve_opts)]),

@@ -59,8 +59,10 @@ def hf_scf_opts_default() -> hf_scf_opts:
 
 
 def jk_opts(schwarz_tau: Optional[float] = None, fp32_bound: Optional[float] = None, host: bool = False,
-            fp32_boys: bool = False, df64: bool = False) -> hf_jk_opts:
+            fp32_boys: bool = False, df64: bool = False, deterministic: bool = False) -> hf_jk_opts:
     o = hf_jk_opts_default()
+    if deterministic:
+        o.flags |= _abi.HF_JK_DETERMINISTIC
     if schwarz_tau is not None:
         o.schwarz_tau = schwarz_tau
     if fp32_bound is not None:
@@ -97,6 +99,10 @@ class Context:
 
     def inject_alloc_failure(self, n: int):
         _lib().hf_ctx_inject_alloc_failure(self._h, n)
+
+    def set_log(self, path: Optional[str]):
+        """JSON-lines log of every SCF iteration ("-" = stderr, None = off)."""
+        _check(_lib().hf_ctx_set_log(self._h, None if path is None else path.encode()), "hf_ctx_set_log")
 
     def close(self):
         if self._h:
@@ -264,6 +270,12 @@ class Basis:
                          diis_error=r.diis_error, homo_lumo_gap=r.homo_lumo_gap, iterations=r.iterations,
                          converged=bool(r.converged), fock_builds=r.fock_builds, quartets=r.quartets,
                          seconds=r.seconds, tensors=out)
+
+    def mp2_energy(self, Cmo, eps, n_occ: int) -> float:
+        """E(2) from MO coefficients Cmo[mu][p] and ascending orbital energies eps (CUDA tensors)."""
+        e2 = C.c_double()
+        _check(_lib().hf_mp2_energy(self._h, _ptr(Cmo), _ptr(eps), int(n_occ), C.byref(e2)), "hf_mp2_energy")
+        return float(e2.value)
 
     def fock_jk_uhf(self, Da, Db, opts: Optional[hf_jk_opts] = None):
         """J[Da + Db], K[Da], K[Db] (CUDA tensors) from one integral evaluation."""
@@ -467,6 +479,10 @@ def hf_uhf_solve(basis: Basis, n_alpha: int, n_beta: int, **kw) -> UHFResult:
 
 def hf_fock_jk_uhf(basis: Basis, Da, Db, opts: Optional[hf_jk_opts] = None):
     return basis.fock_jk_uhf(Da, Db, opts)
+
+
+def hf_mp2_energy(basis: Basis, C_mo, eps, n_occ: int) -> float:
+    return basis.mp2_energy(C_mo, eps, n_occ)
 
 
 def hf_scf_solve_batch(bases, **kw):

@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libhf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # heaviest first, so the long compiles start early
 SOURCES = ["eri_d6.cu", "eri_d5.cu", "eri_d4.cu", "eri_d3.cu", "eri_d2.cu", "eri_d1.cu", "eri_sp.cu",
-           "api.cu", "basis.cu", "onee.cu", "scf.cu", "batch.cu", "serve.cu", "noalloc.cu", "multi.cu"]
+           "api.cu", "basis.cu", "onee.cu", "scf.cu", "batch.cu", "serve.cu", "noalloc.cu", "multi.cu", "mp2.cu"]
 KERNEL_HEADERS = ["eri.cuh", "eri_classes.cuh", "hf_device.h"]
 HEADERS = KERNEL_HEADERS + ["hf_internal.h", "scf_internal.h", "multi.h", "../../include/hf.h"]
 LMAX = 2
@@ -50,9 +50,9 @@ def _stamp(src, flags):
     return h.hexdigest()
 
 
-def _compile(src, flags, verbose):
+def _compile(src, flags, verbose, out_dir=OUT):
     path = os.path.join(CSRC, src)
-    obj = os.path.join(OUT, src.replace(".cu", ".o"))
+    obj = os.path.join(out_dir, src.replace(".cu", ".o"))
     stamp_file = obj + ".stamp"
     st = _stamp(path, flags)
     if os.path.exists(obj) and os.path.exists(stamp_file) and open(stamp_file).read() == st:
@@ -68,25 +68,34 @@ def _compile(src, flags, verbose):
     return obj, True
 
 
-def build(verbose: bool = False, jobs: int | None = None, extra_flags=()) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, extra_flags=(), out_dir: str = OUT,
+          lib: str = LIB) -> str:
+    os.makedirs(out_dir, exist_ok=True)
     subprocess.run([sys.executable, os.path.join(CSRC, "gen_eri.py"),
                     os.path.join(CSRC, "eri_classes.cuh"), str(LMAX)], check=True)
     flags = _flags(extra_flags)
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     jobs = jobs or min(len(srcs), max(2, os.cpu_count() or 2))
     with ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(lambda s: _compile(s, flags, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, flags, verbose, out_dir), srcs))
     objs = [o for o, _ in results]
-    rebuilt = any(r for _, r in results) or not os.path.exists(LIB)
+    rebuilt = any(r for _, r in results) or not os.path.exists(lib)
     if rebuilt:
-        tmp = LIB + f".tmp{os.getpid()}"
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcublas", "-lcusolver"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
+
+
+def build_bounds_checked(verbose: bool = False) -> str:
+    """The same library with -DHF_BOUNDS_CHECK (every index of the J/K
+    kernels checked before use) as libhf_bcheck.so, objects in _build_bcheck/.
+    Load it with HF_LIB=<path> for small test cases."""
+    return build(verbose, extra_flags=("-DHF_BOUNDS_CHECK",), out_dir=os.path.join(HERE, "_build_bcheck"),
+                 lib=os.path.join(HERE, "libhf_bcheck.so"))
 
 
 if __name__ == "__main__":

@@ -219,6 +219,14 @@ extern "C" int hf_ctx_create(hf_ctx** out, int device, size_t hbm_budget, void* 
       if (!c->ops[k].jk64) { rc = hf_fail(HF_ERR_CUDA, "class %d has no kernels", k); break; }
     if (rc != HF_OK) break;
     rc = hf_boys_tables(c);
+    if (rc != HF_OK) break;
+    void* bp = nullptr;
+    rc = hf_dev_alloc(c, &bp, 2 * sizeof(int));
+    if (rc != HF_OK) break;
+    c->bounds = static_cast<int*>(bp);
+    if (cudaMemsetAsync(c->bounds, 0, 2 * sizeof(int), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      rc = hf_fail(HF_ERR_CUDA, "bounds status");
   } while (0);
   if (rc != HF_OK) {
     hf_ctx_destroy(c);
@@ -230,10 +238,19 @@ extern "C" int hf_ctx_create(hf_ctx** out, int device, size_t hbm_budget, void* 
 
 extern "C" void hf_ctx_destroy(hf_ctx* c) {
   if (!c) return;
+  // bases still alive free their memory through this context: the last of
+  // them completes the teardown
+  c->destroy_pending.store(true);
+  if (c->live_bases.load() > 0) return;
+  hf_ctx_teardown(c);
+}
+
+void hf_ctx_teardown(hf_ctx* c) {
   cudaSetDevice(c->device);
   if (c->boys64) hf_dev_free(c, c->boys64, 0);
   if (c->boys32) hf_dev_free(c, c->boys32, 0);
   if (c->boysdf) hf_dev_free(c, c->boysdf, 0);
+  if (c->bounds) hf_dev_free(c, c->bounds, 0);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (int k = 0; k < hf_ctx::kSide; ++k) {
     if (c->side[k]) cudaStreamDestroy(c->side[k]);
@@ -243,7 +260,75 @@ extern "C" void hf_ctx_destroy(hf_ctx* c) {
   if (c->cublas) cublasDestroy(c->cublas);
   if (c->cusolver) cusolverDnDestroy(c->cusolver);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->log && c->own_log) fclose(c->log);
   delete c;
+}
+
+int hf_bounds_status(hf_ctx* c, const char* where) {
+#ifdef HF_BOUNDS_CHECK
+  int st[2] = {0, 0};
+  HF_CUDA(cudaMemcpyAsync(st, c->bounds, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  HF_CUDA(cudaStreamSynchronize(c->stream));
+  if (st[0] != 0) {
+    HF_CUDA(cudaMemsetAsync(c->bounds, 0, sizeof st, c->stream));
+    static const char* names[] = {"", "work item", "shell pair", "primitive record", "matrix element", "Boys row"};
+    return hf_fail(HF_ERR_INVALID, "%s: bounds check failed: %s index %d", where,
+                   st[0] > 0 && st[0] < 6 ? names[st[0]] : "?", st[1]);
+  }
+#else
+  (void)c;
+  (void)where;
+#endif
+  return HF_OK;
+}
+
+extern "C" int hf_bounds_checked(void) {
+#ifdef HF_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+extern "C" int hf_ctx_set_log(hf_ctx* c, const char* path) {
+  if (!c) return hf_fail(HF_ERR_INVALID, "hf_ctx_set_log: null context");
+  std::lock_guard<std::mutex> lk(c->log_mu);
+  if (c->log && c->own_log) fclose(c->log);
+  c->log = nullptr;
+  c->own_log = false;
+  if (!path) return HF_OK;
+  if (path[0] == '-' && path[1] == 0) {
+    c->log = stderr;
+    return HF_OK;
+  }
+  FILE* f = fopen(path, "a");
+  if (!f) return hf_fail(HF_ERR_INVALID, "hf_ctx_set_log: cannot open %s", path);
+  c->log = f;
+  c->own_log = true;
+  return HF_OK;
+}
+
+void hf_log_scf_iter(hf_ctx* c, const char* solver, unsigned long long mol, int nbf, int iter, double energy,
+                     double delta_e, double diis_error, double t, int converged) {
+  if (!c || !c->log) return;
+  std::lock_guard<std::mutex> lk(c->log_mu);
+  if (!c->log) return;
+  char de[40];
+  if (delta_e == delta_e) snprintf(de, sizeof de, "%.17g", delta_e);
+  else snprintf(de, sizeof de, "null");
+  fprintf(c->log,
+          "{\"event\": \"scf_iter\", \"solver\": \"%s\", \"mol\": %llu, \"nbf\": %d, \"iter\": %d, "
+          "\"energy\": %.17g, \"delta_e\": %s, \"diis_error\": %.6g, \"t\": %.6f, \"converged\": %d}\n",
+          solver, mol, nbf, iter, energy, de, diis_error, t, converged);
+  fflush(c->log);
+}
+
+void hf_log_line(hf_ctx* c, const char* json) {
+  if (!c || !c->log) return;
+  std::lock_guard<std::mutex> lk(c->log_mu);
+  if (!c->log) return;
+  fprintf(c->log, "%s\n", json);
+  fflush(c->log);
 }
 
 extern "C" void* hf_ctx_stream(hf_ctx* c) { return c ? (void*)c->stream : nullptr; }

@@ -126,6 +126,32 @@ __global__ void symmetrize_jk(const double* Jp, const double* Kp, double* J, dou
   }
 }
 
+// J = 2 (J' + J'^T), K = K' + K'^T (K2 likewise when given) from fixed-point
+// accumulators (two 64-bit words per element, units 2^-20 and 2^-56).
+__device__ __forceinline__ double fixed_value(const unsigned long long* q, size_t i) {
+  return (double)(long long)q[2 * i] * (1.0 / 1048576.0) + (double)(long long)q[2 * i + 1] * 0x1p-56;
+}
+__global__ void finish_fixed(const unsigned long long* __restrict__ Jq, const unsigned long long* __restrict__ Kq,
+                             const unsigned long long* __restrict__ K2q, double* __restrict__ J,
+                             double* __restrict__ K, double* __restrict__ K2, int n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  if (j < i) return;
+  const size_t ij = (size_t)i * n + j, ji = (size_t)j * n + i;
+  const double sj = 2.0 * (fixed_value(Jq, ij) + fixed_value(Jq, ji));
+  const double sk = fixed_value(Kq, ij) + fixed_value(Kq, ji);
+  J[ij] = sj;
+  J[ji] = sj;
+  K[ij] = sk;
+  K[ji] = sk;
+  if (K2) {
+    const double s2 = fixed_value(K2q, ij) + fixed_value(K2q, ji);
+    K2[ij] = s2;
+    K2[ji] = s2;
+  }
+}
+
 // ------------------------------------------------------------- basis create
 extern "C" int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, const hf_shell* shells, int nshell,
                                const double* exps, const double* coefs, int n_electrons, hf_basis** out) {
@@ -154,9 +180,11 @@ extern "C" int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, con
       if (!std::isfinite(atoms[a].xyz[x])) return hf_fail(HF_ERR_INVALID, "atom %d: non-finite coordinate", a);
 
   cudaSetDevice(ctx->device);
+  if (ctx->destroy_pending.load()) return hf_fail(HF_ERR_INVALID, "hf_basis_create: context is being destroyed");
   hf_basis* b = new (std::nothrow) hf_basis();
   if (!b) return hf_fail(HF_ERR_OOM, "host allocation");
   b->ctx = ctx;
+  ctx->live_bases.fetch_add(1);
   b->natom = natom;
   b->nshell = nshell;
   b->nbf = nbf;
@@ -350,9 +378,12 @@ extern "C" int hf_basis_create(hf_ctx* ctx, const hf_atom* atoms, int natom, con
 
 extern "C" void hf_basis_destroy(hf_basis* b) {
   if (!b) return;
-  cudaSetDevice(b->ctx->device);
-  cudaStreamSynchronize(b->ctx->stream);
+  hf_ctx* ctx = b->ctx;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
   delete b;
+  // the last basis of a context whose destroy was called finishes it
+  if (ctx->live_bases.fetch_sub(1) == 1 && ctx->destroy_pending.load()) hf_ctx_teardown(ctx);
 }
 
 extern "C" int hf_basis_nbf(const hf_basis* b) { return b ? b->nbf : 0; }
@@ -361,7 +392,7 @@ extern "C" int hf_basis_nshell(const hf_basis* b) { return b ? b->nshell : 0; }
 extern "C" size_t hf_basis_device_bytes(const hf_basis* b) {
   if (!b) return 0;
   size_t s = b->prim64.bytes() + b->prim32.bytes() + b->primdf.bytes() + b->pinfo.bytes() + b->Q.bytes() + b->ketlist.bytes() +
-             b->counters.bytes() + b->hD.bytes() + b->hJ.bytes() + b->hK.bytes() + b->Dsum.bytes() + b->S.bytes() + b->T.bytes() +
+             b->counters.bytes() + b->hD.bytes() + b->hJ.bytes() + b->hK.bytes() + b->Dsum.bytes() + b->detq.bytes() + b->S.bytes() + b->T.bytes() +
              b->V.bytes();
   for (int c = 0; c < HF_NCLASS; ++c)
     for (const ClassWork* w : {&b->work64[c], &b->work32[c]})
@@ -541,14 +572,30 @@ LaunchShape hf_launch_shape(const hf_ctx* ctx, int occ, int nitems, int cap_per_
 
 int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, double* K, int* counters,
               const hf_jk_opts& o, cudaStream_t st, long long* nq, JKClassTiming* timing, const JKSpin* spin) {
+  NvtxRange nv_build("J/K build");
   hf_ctx* ctx = b->ctx;
   const PairSet ps = hf_pairset(b);
-  const KernelCommon kc = hf_kernel_common(ctx, o.flags);
+  KernelCommon kc = hf_kernel_common(ctx, o.flags);
+  const size_t nn = (size_t)b->nbf * b->nbf;
   MolJK one{D, Jp, Kp, b->nbf, 0};
   if (spin) {
     one.Dj = spin->Dj;
     one.D2 = spin->D2;
     one.K2 = spin->K2;
+  }
+  // deterministic order: the kernels accumulate into fixed-point words
+  // (basis-owned, zeroed here) and finish_fixed writes J, K (and K2)
+  const bool det = (o.flags & HF_JK_DETERMINISTIC) != 0;
+  unsigned long long* q = nullptr;
+  if (det) {
+    const size_t words = 2 * nn * (spin ? 3 : 2);
+    if (b->detq.n < words) HF_CHECK(b->detq.alloc(ctx, words));
+    q = b->detq.ptr;
+    HF_CUDA(cudaMemsetAsync(q, 0, words * sizeof(unsigned long long), st));
+    kc.det = 1;
+    one.J = reinterpret_cast<double*>(q);
+    one.K = reinterpret_cast<double*>(q + 2 * nn);
+    if (spin) one.K2 = reinterpret_cast<double*>(q + 4 * nn);
   }
   long long total = 0;
   if (timing) {
@@ -567,6 +614,7 @@ int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, d
       const jk_launch_fn fn = r == 0 ? hf_jk_hi(op, o.flags) : op.jk32;
       const int occ = r == 0 ? hf_occ_hi(op, o.flags) : op.occ32();
       const LaunchShape sh = hf_launch_shape(ctx, occ, w.nitems);
+      NvtxRange nv_cls(op.name);
       fn(w, ps, kc, one, nullptr, sh.grid, sh.threads, st);
       if (timing) {
         timing->which[timing->n - 1] = 2 * c + r;
@@ -575,10 +623,14 @@ int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, d
     }
   }
   HF_CUDA(cudaGetLastError());
-  const size_t nn = (size_t)b->nbf * b->nbf;
   double* K2 = spin ? spin->K2 : nullptr;
-  symmetrize_jk<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Jp, Kp, J, K, K2, K2, b->nbf);
+  if (det)
+    finish_fixed<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(q, q + 2 * nn, spin ? q + 4 * nn : nullptr, J, K, K2,
+                                                               b->nbf);
+  else
+    symmetrize_jk<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Jp, Kp, J, K, K2, K2, b->nbf);
   HF_CUDA(cudaGetLastError());
+  HF_CHECK(hf_bounds_status(ctx, "J/K build"));
   if (nq) *nq = total;
   return HF_OK;
 }

@@ -33,6 +33,7 @@ extern "C" int hf_scf_solve_batch(hf_basis* const* bases, int count, const hf_sc
   if (opts) o = *opts;
   if (o.max_iter < 1 || o.diis_size < 0 || !(o.e_tol >= 0.0) || (o.flags & HF_SCF_STORED_ERI) || o.D0)
     return hf_fail(HF_ERR_INVALID, "hf_scf_solve_batch: bad options (stored ERI and D0 are single-molecule only)");
+  HF_CHECK(hf_reject_deterministic(o.jk.flags, "hf_scf_solve_batch"));
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
   const auto t0 = std::chrono::steady_clock::now();
@@ -64,6 +65,7 @@ extern "C" int hf_scf_solve_batch(hf_basis* const* bases, int count, const hf_sc
   int nactive = 0;
   for (int a : active) nactive += a;
   while (nactive > 0) {
+    NvtxRange nv("scf iteration (batch)");
     for (int i = 0; i < count; ++i)
       if (active[i]) HF_CHECK(scf_density(mols[i], *S[i]));
     if (!mj.tuned) {
@@ -85,7 +87,11 @@ extern "C" int hf_scf_solve_batch(hf_basis* const* bases, int count, const hf_sc
     for (int i = 0; i < count; ++i) {
       if (!active[i]) continue;
       HF_CHECK(scf_diis_step(mols[i], *S[i]));
-      if (scf_after_iter(mols[i], *S[i], o)) {
+      const bool done = scf_after_iter(mols[i], *S[i], o);
+      hf_log_scf_iter(ctx, "batch", (unsigned long long)i, mols[i]->nbf, S[i]->iter, S[i]->energy, S[i]->delta_e,
+                      S[i]->diis_error, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(),
+                      S[i]->converged);
+      if (done) {
         HF_CHECK(scf_finish(mols[i], *S[i], &results[i]));
         status[i] = S[i]->converged ? HF_OK : HF_ERR_NOT_CONVERGED;
         if (!S[i]->converged && first_error == HF_OK) first_error = HF_ERR_NOT_CONVERGED;

@@ -347,7 +347,34 @@ __device__ __forceinline__ constexpr double comp_scale(int l, int c) {
   return (l == 2 && (c == 1 || c == 2 || c == 4)) ? 1.7320508075688772935 : 1.0;
 }
 
+// One contribution v to element idx of an accumulator.  Default: an FP64
+// atomic add into base[idx].  Deterministic mode (HF_JK_DETERMINISTIC): base
+// holds two 64-bit integers per element and v goes in as fixed point,
+// hi = trunc(v 2^20) and lo = rint((v 2^20 - hi) 2^36), with integer atomic
+// adds; integer addition is associative, so the sums, and J and K after
+// the conversion back (hi 2^-20 + lo 2^-56), do not depend on the order in
+// which the warps finish.  Resolution 2^-57 per contribution; lo stays in
+// range for up to 2^27 contributions to one element.
+__device__ __forceinline__ void jk_acc(double* base, size_t idx, double v, int det) {
+  if (!det) {
+    atomicAdd(base + idx, v);
+    return;
+  }
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(base) + 2 * idx;
+  const double sc = v * 1048576.0;  // 2^20
+  const double h = trunc(sc);
+  const long long hi = (long long)h;
+  const long long lo = __double2ll_rn((sc - h) * 68719476736.0);  // 2^36
+  if (hi) atomicAdd(q, (unsigned long long)hi);
+  if (lo) atomicAdd(q + 1, (unsigned long long)lo);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -384,10 +411,28 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
     const int rr = t - __ldg(w.ioff + bi);
     const int kblk = rr / nsp, part = rr - kblk * nsp;
     const int kidx = __ldg(w.kbeg + bi) + 32 * kblk + lane;
-    const bool active = kidx < __ldg(w.kend + bi);
-    const int kp = active ? __ldg(ketb + kidx) : bp;
+    if (!HF_BCHECK(kc, bp >= 0 && bp < P.npairs, HF_BC_PAIR, bp)) continue;
+    bool active = kidx < __ldg(w.kend + bi);
+    if (active && !HF_BCHECK(kc, kidx >= 0, HF_BC_ITEM, kidx)) active = false;
+    int kp = active ? __ldg(ketb + kidx) : bp;
+    if (active && !HF_BCHECK(kc, kp >= 0 && kp < P.npairs, HF_BC_PAIR, kp)) {
+      active = false;
+      kp = bp;
+    }
     const PairInfo bra = P.info[bp];
     const PairInfo ket = P.info[kp];
+    {
+      const int nbf_ = mjp ? mjp->nbf : one.nbf;
+      (void)nbf_;
+      const bool bra_ok = HF_BCHECK(kc, bra.prim0 >= 0 && bra.prim0 + bra.nprim <= P.nprimpairs, HF_BC_PRIM,
+                                    bra.prim0) &&
+                          HF_BCHECK(kc, bra.bfA + NA <= nbf_ && bra.bfB + NB <= nbf_, HF_BC_MAT, bra.bfA);
+      if (!bra_ok) continue;  // warp-uniform
+      if (active && !(HF_BCHECK(kc, ket.prim0 >= 0 && ket.prim0 + ket.nprim <= P.nprimpairs, HF_BC_PRIM,
+                                ket.prim0) &&
+                      HF_BCHECK(kc, ket.bfA + NC <= nbf_ && ket.bfB + ND <= nbf_, HF_BC_MAT, ket.bfA)))
+        active = false;
+    }
     // this part's bra primitive pairs (all of them unless the item is split;
     // the contraction is linear, so the parts' digested blocks add up)
     const int ib0 = part * bra.nprim / nsp, ib1 = (part + 1) * bra.nprim / nsp;
@@ -408,46 +453,50 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
     double* __restrict__ J = mo.J;
     const int nbf = mo.nbf;
     const int nspin = mo.D2 ? 2 : 1;
-    double wdeg = active ? 1.0 : 0.0;
-    if (bra.same) wdeg *= 0.5;
-    if (ket.same) wdeg *= 0.5;
-    if (bp == kp) wdeg *= 0.5;
+    // digestion arithmetic: FP32 for the reduced-precision quartets (their
+    // integrals carry FP32 error already), FP64 otherwise; every sum is added
+    // into the FP64 J and K
+    using A = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
+    A wdeg = active ? (A)1 : (A)0;
+    if (bra.same) wdeg *= (A)0.5;
+    if (ket.same) wdeg *= (A)0.5;
+    if (bp == kp) wdeg *= (A)0.5;
 
     const int a0 = bra.bfA, b0 = bra.bfB, c0 = ket.bfA, d0 = ket.bfB;
     // J'_ab = w sum_cd I D_cd  (warp-reduced: the bra is uniform over the warp)
-    double Dcd[NC * ND];
+    A Dcd[NC * ND];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
       for (int d = 0; d < ND; ++d)
-        Dcd[c * ND + d] = active ? __ldg(Dj + (size_t)(c0 + c) * nbf + d0 + d) * comp_scale(C::LC, c) * comp_scale(C::LD, d) : 0.0;
+        Dcd[c * ND + d] = active ? (A)__ldg(Dj + (size_t)(c0 + c) * nbf + d0 + d) * (A)comp_scale(C::LC, c) * (A)comp_scale(C::LD, d) : (A)0;
 #pragma unroll
     for (int a = 0; a < NA; ++a)
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        double s = 0.0;
+        A s = (A)0;
 #pragma unroll
-        for (int cd = 0; cd < NC * ND; ++cd) s = fma((double)I[(a * NB + b) * NC * ND + cd], Dcd[cd], s);
+        for (int cd = 0; cd < NC * ND; ++cd) s = fma((A)I[(a * NB + b) * NC * ND + cd], Dcd[cd], s);
         s = warp_sum(s * wdeg);
         if (lane == 0 && s != 0.0)
-          atomicAdd(J + (size_t)(a0 + a) * nbf + b0 + b, s * comp_scale(C::LA, a) * comp_scale(C::LB, b));
+          jk_acc(J, (size_t)(a0 + a) * nbf + b0 + b, (double)(s * (A)comp_scale(C::LA, a) * (A)comp_scale(C::LB, b)), kc.det);
       }
     if (!active) continue;
     // J'_cd = w sum_ab I D_ab
-    double Dab[NA * NB];
+    A Dab[NA * NB];
 #pragma unroll
     for (int a = 0; a < NA; ++a)
 #pragma unroll
       for (int b = 0; b < NB; ++b)
-        Dab[a * NB + b] = __ldg(Dj + (size_t)(a0 + a) * nbf + b0 + b) * comp_scale(C::LA, a) * comp_scale(C::LB, b);
+        Dab[a * NB + b] = (A)__ldg(Dj + (size_t)(a0 + a) * nbf + b0 + b) * (A)comp_scale(C::LA, a) * (A)comp_scale(C::LB, b);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
       for (int d = 0; d < ND; ++d) {
-        double s = 0.0;
+        A s = (A)0;
 #pragma unroll
-        for (int ab = 0; ab < NA * NB; ++ab) s = fma((double)I[ab * NC * ND + c * ND + d], Dab[ab], s);
-        atomicAdd(J + (size_t)(c0 + c) * nbf + d0 + d, s * wdeg * comp_scale(C::LC, c) * comp_scale(C::LD, d));
+        for (int ab = 0; ab < NA * NB; ++ab) s = fma((A)I[ab * NC * ND + c * ND + d], Dab[ab], s);
+        jk_acc(J, (size_t)(c0 + c) * nbf + d0 + d, (double)(s * wdeg * (A)comp_scale(C::LC, c) * (A)comp_scale(C::LD, d)), kc.det);
       }
     // exchange of each spin: K from D, and K2 from D2 in two-spin builds
 #pragma unroll 1
@@ -456,69 +505,69 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
     double* __restrict__ Kx = sp ? mo.K2 : mo.K;
     // K'_ac = w sum_bd I D_bd ;  K'_ad = w sum_bc I D_bc
     {
-      double Dbd[NB * ND], Dbc[NB * NC];
+      A Dbd[NB * ND], Dbc[NB * NC];
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
 #pragma unroll
         for (int d = 0; d < ND; ++d)
-          Dbd[b * ND + d] = __ldg(D + (size_t)(b0 + b) * nbf + d0 + d) * comp_scale(C::LB, b) * comp_scale(C::LD, d);
+          Dbd[b * ND + d] = (A)__ldg(D + (size_t)(b0 + b) * nbf + d0 + d) * (A)comp_scale(C::LB, b) * (A)comp_scale(C::LD, d);
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-          Dbc[b * NC + c] = __ldg(D + (size_t)(b0 + b) * nbf + c0 + c) * comp_scale(C::LB, b) * comp_scale(C::LC, c);
+          Dbc[b * NC + c] = (A)__ldg(D + (size_t)(b0 + b) * nbf + c0 + c) * (A)comp_scale(C::LB, b) * (A)comp_scale(C::LC, c);
       }
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          double s = 0.0;
+          A s = (A)0;
 #pragma unroll
           for (int b = 0; b < NB; ++b)
 #pragma unroll
-            for (int d = 0; d < ND; ++d) s = fma((double)I[((a * NB + b) * NC + c) * ND + d], Dbd[b * ND + d], s);
-          atomicAdd(Kx + (size_t)(a0 + a) * nbf + c0 + c, s * wdeg * comp_scale(C::LA, a) * comp_scale(C::LC, c));
+            for (int d = 0; d < ND; ++d) s = fma((A)I[((a * NB + b) * NC + c) * ND + d], Dbd[b * ND + d], s);
+          jk_acc(Kx, (size_t)(a0 + a) * nbf + c0 + c, (double)(s * wdeg * (A)comp_scale(C::LA, a) * (A)comp_scale(C::LC, c)), kc.det);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-          double s = 0.0;
+          A s = (A)0;
 #pragma unroll
           for (int b = 0; b < NB; ++b)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) s = fma((double)I[((a * NB + b) * NC + c) * ND + d], Dbc[b * NC + c], s);
-          atomicAdd(Kx + (size_t)(a0 + a) * nbf + d0 + d, s * wdeg * comp_scale(C::LA, a) * comp_scale(C::LD, d));
+            for (int c = 0; c < NC; ++c) s = fma((A)I[((a * NB + b) * NC + c) * ND + d], Dbc[b * NC + c], s);
+          jk_acc(Kx, (size_t)(a0 + a) * nbf + d0 + d, (double)(s * wdeg * (A)comp_scale(C::LA, a) * (A)comp_scale(C::LD, d)), kc.det);
         }
       }
     }
     // K'_bc = w sum_ad I D_ad ;  K'_bd = w sum_ac I D_ac
     {
-      double Dad[NA * ND], Dac[NA * NC];
+      A Dad[NA * ND], Dac[NA * NC];
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
 #pragma unroll
         for (int d = 0; d < ND; ++d)
-          Dad[a * ND + d] = __ldg(D + (size_t)(a0 + a) * nbf + d0 + d) * comp_scale(C::LA, a) * comp_scale(C::LD, d);
+          Dad[a * ND + d] = (A)__ldg(D + (size_t)(a0 + a) * nbf + d0 + d) * (A)comp_scale(C::LA, a) * (A)comp_scale(C::LD, d);
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-          Dac[a * NC + c] = __ldg(D + (size_t)(a0 + a) * nbf + c0 + c) * comp_scale(C::LA, a) * comp_scale(C::LC, c);
+          Dac[a * NC + c] = (A)__ldg(D + (size_t)(a0 + a) * nbf + c0 + c) * (A)comp_scale(C::LA, a) * (A)comp_scale(C::LC, c);
       }
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          double s = 0.0;
+          A s = (A)0;
 #pragma unroll
           for (int a = 0; a < NA; ++a)
 #pragma unroll
-            for (int d = 0; d < ND; ++d) s = fma((double)I[((a * NB + b) * NC + c) * ND + d], Dad[a * ND + d], s);
-          atomicAdd(Kx + (size_t)(b0 + b) * nbf + c0 + c, s * wdeg * comp_scale(C::LB, b) * comp_scale(C::LC, c));
+            for (int d = 0; d < ND; ++d) s = fma((A)I[((a * NB + b) * NC + c) * ND + d], Dad[a * ND + d], s);
+          jk_acc(Kx, (size_t)(b0 + b) * nbf + c0 + c, (double)(s * wdeg * (A)comp_scale(C::LB, b) * (A)comp_scale(C::LC, c)), kc.det);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-          double s = 0.0;
+          A s = (A)0;
 #pragma unroll
           for (int a = 0; a < NA; ++a)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) s = fma((double)I[((a * NB + b) * NC + c) * ND + d], Dac[a * NC + c], s);
-          atomicAdd(Kx + (size_t)(b0 + b) * nbf + d0 + d, s * wdeg * comp_scale(C::LB, b) * comp_scale(C::LD, d));
+            for (int c = 0; c < NC; ++c) s = fma((A)I[((a * NB + b) * NC + c) * ND + d], Dac[a * NC + c], s);
+          jk_acc(Kx, (size_t)(b0 + b) * nbf + d0 + d, (double)(s * wdeg * (A)comp_scale(C::LB, b) * (A)comp_scale(C::LD, d)), kc.det);
         }
       }
     }
@@ -572,20 +621,148 @@ __device__ __forceinline__ double comp_scale_rt(int l, int c) {
   return (l == 2 && (c == 1 || c == 2 || c == 4)) ? 1.7320508075688772935 : 1.0;
 }
 
+// The contracted Cartesian block of one shell quartet (bra|ket) over its
+// primitive quartets [q_lo, q_hi), by one warp, in the scheme described
+// above; on return the warp's shared memory s holds it after the [e0|f0]
+// and the bra HRR rows: as doubles pre-multiplied by the d-component scales
+// (R = double or df64) or as floats (R = float), at s + NT + NAB * NF.
+template <class C, typename R, typename PB>
+__device__ __forceinline__ void coop_block(const PB* __restrict__ pbase, const KernelCommon& kc, const PairInfo& bra,
+                                           const PairInfo& ket, int q_lo, int nq, R* const s, const int G,
+                                           const int lane) {
+  using S = CoopSizes<C>;
+  constexpr int NB = C::NB, NC = C::NC, ND = C::ND, NE = C::NE, NF = C::NF;
+  constexpr int NT = S::NT, NAB = S::NAB, NCD = S::NCD, NK = (NT + 31) / 32;
+  (void)NC;
+  (void)ND;
+  R* const stage = s + C::NSLOT;
+  const uint4* __restrict__ nodes = hfgen::CoopTables<C>::nodes();
+  const int* __restrict__ levels = hfgen::CoopTables<C>::levels();
+  const unsigned short* __restrict__ tgt = hfgen::CoopTables<C>::targets();
+  R acc[NK];
+#pragma unroll
+  for (int k = 0; k < NK; ++k) acc[k] = (R)0;
+  for (int g0 = q_lo; g0 < nq; g0 += G) {
+    const int q = g0 + lane;
+    if (lane < G && q < nq) {
+      const int ib = q / ket.nprim, ik = q - ib * ket.nprim;
+      R* const cv = stage + lane * S::ROW;
+      Prim<R> a, c;
+      load_prim(pbase, bra.prim0 + ib, a);
+      load_prim(pbase, ket.prim0 + ik, c);
+      const R pq = a.p + c.p;
+      const R rs = (R)rsqrt(pq);
+      const R inv = rs * rs;
+      const R rp = c.p * inv, rq = a.p * inv;
+      R PQ[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        PQ[i] = a.P[i] - c.P[i];
+        cv[1 + i] = a.PA[i];
+        cv[4 + i] = -rp * PQ[i];
+        cv[7 + i] = c.PA[i];
+        cv[10 + i] = rq * PQ[i];
+      }
+      cv[0] = (R)0;
+      cv[13] = rp;
+      cv[14] = rq;
+      const R o2pq = (R)0.5 * inv;
+#pragma unroll
+      for (int k = 1; k <= 8; ++k) {
+        cv[14 + k] = (R)k * a.o2p;
+        cv[22 + k] = (R)k * c.o2p;
+        cv[30 + k] = (R)k * o2pq;
+      }
+      const R T = a.p * rp * (PQ[0] * PQ[0] + PQ[1] * PQ[1] + PQ[2] * PQ[2]);
+      R B[C::L + 1];
+      BoysSel<C::L, R>::eval(T, kc, B);
+      const R pref = a.K * c.K * rs;
+#pragma unroll
+      for (int m = 0; m <= C::L; ++m) cv[HF_NCOEF + m] = B[m] * pref;
+    }
+    __syncwarp();
+    const int ng = min(G, nq - g0);  // rows set up in this pass
+    for (int jq = 0; jq < ng; ++jq) {
+      const R* const cv = stage + jq * S::ROW;
+      if (lane <= C::L) s[lane] = cv[HF_NCOEF + lane];
+      __syncwarp();
+      for (int lev = 0; lev < C::NLEV; ++lev) {
+        const int n1 = __ldg(levels + lev);
+        for (int n = (lev == 0 ? 0 : __ldg(levels + lev - 1)) + lane; n < n1; n += 32) {
+          const uint4 d = __ldg(nodes + n);
+          const unsigned c = d.w;
+          R v = fmac(cv[(c >> 6) & 63u], s[d.y & 0xffffu], cv[c & 63u] * s[d.x >> 16]);
+          if (c & (1u << 30))
+            v = fmac(cv[(c >> 12) & 63u], fmac(-cv[(c >> 18) & 63u], s[d.z & 0xffffu], s[d.y >> 16]), v);
+          if (c & (1u << 31)) v = fmac(cv[(c >> 24) & 63u], s[d.z >> 16], v);
+          s[d.x & 0xffffu] = v;
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int k = 0; k < NK; ++k) {
+        const int tt = lane + 32 * k;
+        if (tt < NT) acc[k] += s[__ldg(tgt + tt)];
+      }
+      __syncwarp();
+    }
+  }
+  // contracted [e0|f0] -> shared memory, then HRR
+  R* const A = s;
+  R* const H = s + NT;
+  R* const I = H + NAB * NF;
+  constexpr bool kPre = sizeof(R) == sizeof(double);      // R = double or df64
+  double* const Id = reinterpret_cast<double*>(I);        // same storage when kPre
+#pragma unroll
+  for (int k = 0; k < NK; ++k) {
+    const int tt = lane + 32 * k;
+    if (tt < NT) A[tt] = acc[k];
+  }
+  __syncwarp();
+  {
+    const R AB[3] = {(R)bra.AB[0], (R)bra.AB[1], (R)bra.AB[2]};
+    for (int f = lane; f < NF; f += 32) {
+      R x[NE], y[NAB];
+#pragma unroll
+      for (int e = 0; e < NE; ++e) x[e] = A[e * NF + f];
+      C::template hrr_bra_row<R>(x, y, AB);
+#pragma unroll
+      for (int ab = 0; ab < NAB; ++ab) H[ab * NF + f] = y[ab];
+    }
+  }
+  __syncwarp();
+  {
+    const R CD[3] = {(R)ket.AB[0], (R)ket.AB[1], (R)ket.AB[2]};
+    for (int ab = lane; ab < NAB; ab += 32) {
+      R x[NF], y[NCD];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) x[f] = H[ab * NF + f];
+      C::template hrr_ket_row<R>(x, y, CD);
+      if constexpr (kPre) {
+        // FP64 and df64: stored once as a double, already multiplied by the
+        // d-component scales s_a s_b s_c s_d that every contraction needs
+        const double sab = comp_scale_rt(C::LA, ab / NB) * comp_scale_rt(C::LB, ab % NB);
+#pragma unroll
+        for (int cd = 0; cd < NCD; ++cd)
+          Id[ab * NCD + cd] = (double)y[cd] * (sab * comp_scale_rt(C::LC, cd / ND) * comp_scale_rt(C::LD, cd % ND));
+      } else {
+#pragma unroll
+        for (int cd = 0; cd < NCD; ++cd) I[ab * NCD + cd] = y[cd];
+      }
+    }
+  }
+}
+
 template <class C, typename R>
 __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const PairSet ps, const KernelCommon kc,
                                                           const MolJK one, const MolJK* __restrict__ mols,
                                                           const int G) {
   using S = CoopSizes<C>;
   constexpr int NB = C::NB, NC = C::NC, ND = C::ND, NE = C::NE, NF = C::NF;
-  constexpr int NT = S::NT, NAB = S::NAB, NCD = S::NCD, NK = (NT + 31) / 32;
+  constexpr int NT = S::NT, NAB = S::NAB, NCD = S::NCD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* const s = reinterpret_cast<R*>(smem_raw) + (threadIdx.x >> 5) * S::ws(G);
-  R* const stage = s + C::NSLOT;
   const int lane = threadIdx.x & 31;
-  const uint4* __restrict__ nodes = hfgen::CoopTables<C>::nodes();
-  const int* __restrict__ levels = hfgen::CoopTables<C>::levels();
-  const unsigned short* __restrict__ tgt = hfgen::CoopTables<C>::targets();
   const auto* base = PrimBase<R>::get(ps);
   for (;;) {
     int t = 0;
@@ -608,124 +785,28 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
     const int rr = t - __ldg(w.ioff + bi);
     const int kj = rr / nsp, part = rr - kj * nsp;
     const int kp = __ldg(ketb + __ldg(w.kbeg + bi) + kj);
+    if (!HF_BCHECK(kc, bp >= 0 && bp < P.npairs, HF_BC_PAIR, bp)) continue;
+    if (!HF_BCHECK(kc, kp >= 0 && kp < P.npairs, HF_BC_PAIR, kp)) continue;
     const PairInfo bra = P.info[bp];
     const PairInfo ket = P.info[kp];
-    R acc[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) acc[k] = (R)0;
+    {
+      const int nbf_ = mjp ? mjp->nbf : one.nbf;
+      (void)nbf_;
+      const bool ok =
+          HF_BCHECK(kc, bra.prim0 >= 0 && bra.prim0 + bra.nprim <= P.nprimpairs, HF_BC_PRIM, bra.prim0) &&
+          HF_BCHECK(kc, ket.prim0 >= 0 && ket.prim0 + ket.nprim <= P.nprimpairs, HF_BC_PRIM, ket.prim0) &&
+          HF_BCHECK(kc, bra.bfA + C::NA <= nbf_ && bra.bfB + NB <= nbf_, HF_BC_MAT, bra.bfA) &&
+          HF_BCHECK(kc, ket.bfA + NC <= nbf_ && ket.bfB + ND <= nbf_, HF_BC_MAT, ket.bfA);
+      if (!ok) continue;  // warp-uniform: one quartet per warp
+    }
     // this part's primitive quartets (all unless the item is split; the
     // parts' digested blocks add up)
     const int nq_all = bra.nprim * ket.nprim;
     const int q_lo = part * nq_all / nsp, nq = (part + 1) * nq_all / nsp;
-    for (int g0 = q_lo; g0 < nq; g0 += G) {
-      const int q = g0 + lane;
-      if (lane < G && q < nq) {
-        const int ib = q / ket.nprim, ik = q - ib * ket.nprim;
-        R* const cv = stage + lane * S::ROW;
-        Prim<R> a, c;
-        load_prim(pbase, bra.prim0 + ib, a);
-        load_prim(pbase, ket.prim0 + ik, c);
-        const R pq = a.p + c.p;
-        const R rs = (R)rsqrt(pq);
-        const R inv = rs * rs;
-        const R rp = c.p * inv, rq = a.p * inv;
-        R PQ[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          PQ[i] = a.P[i] - c.P[i];
-          cv[1 + i] = a.PA[i];
-          cv[4 + i] = -rp * PQ[i];
-          cv[7 + i] = c.PA[i];
-          cv[10 + i] = rq * PQ[i];
-        }
-        cv[0] = (R)0;
-        cv[13] = rp;
-        cv[14] = rq;
-        const R o2pq = (R)0.5 * inv;
-#pragma unroll
-        for (int k = 1; k <= 8; ++k) {
-          cv[14 + k] = (R)k * a.o2p;
-          cv[22 + k] = (R)k * c.o2p;
-          cv[30 + k] = (R)k * o2pq;
-        }
-        const R T = a.p * rp * (PQ[0] * PQ[0] + PQ[1] * PQ[1] + PQ[2] * PQ[2]);
-        R B[C::L + 1];
-        BoysSel<C::L, R>::eval(T, kc, B);
-        const R pref = a.K * c.K * rs;
-#pragma unroll
-        for (int m = 0; m <= C::L; ++m) cv[HF_NCOEF + m] = B[m] * pref;
-      }
-      __syncwarp();
-      const int ng = min(G, nq - g0);  // rows set up in this pass
-      for (int jq = 0; jq < ng; ++jq) {
-        const R* const cv = stage + jq * S::ROW;
-        if (lane <= C::L) s[lane] = cv[HF_NCOEF + lane];
-        __syncwarp();
-        for (int lev = 0; lev < C::NLEV; ++lev) {
-          const int n1 = __ldg(levels + lev);
-          for (int n = (lev == 0 ? 0 : __ldg(levels + lev - 1)) + lane; n < n1; n += 32) {
-            const uint4 d = __ldg(nodes + n);
-            const unsigned c = d.w;
-            R v = fmac(cv[(c >> 6) & 63u], s[d.y & 0xffffu], cv[c & 63u] * s[d.x >> 16]);
-            if (c & (1u << 30))
-              v = fmac(cv[(c >> 12) & 63u], fmac(-cv[(c >> 18) & 63u], s[d.z & 0xffffu], s[d.y >> 16]), v);
-            if (c & (1u << 31)) v = fmac(cv[(c >> 24) & 63u], s[d.z >> 16], v);
-            s[d.x & 0xffffu] = v;
-          }
-          __syncwarp();
-        }
-#pragma unroll
-        for (int k = 0; k < NK; ++k) {
-          const int tt = lane + 32 * k;
-          if (tt < NT) acc[k] += s[__ldg(tgt + tt)];
-        }
-        __syncwarp();
-      }
-    }
-    // contracted [e0|f0] -> shared memory, then HRR
-    R* const A = s;
-    R* const H = s + NT;
-    R* const I = H + NAB * NF;
+    coop_block<C, R>(pbase, kc, bra, ket, q_lo, nq, s, G, lane);
+    R* const I = s + NT + NAB * NF;
     constexpr bool kPre = sizeof(R) == sizeof(double);      // R = double or df64
     double* const Id = reinterpret_cast<double*>(I);        // same storage when kPre
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-      const int tt = lane + 32 * k;
-      if (tt < NT) A[tt] = acc[k];
-    }
-    __syncwarp();
-    {
-      const R AB[3] = {(R)bra.AB[0], (R)bra.AB[1], (R)bra.AB[2]};
-      for (int f = lane; f < NF; f += 32) {
-        R x[NE], y[NAB];
-#pragma unroll
-        for (int e = 0; e < NE; ++e) x[e] = A[e * NF + f];
-        C::template hrr_bra_row<R>(x, y, AB);
-#pragma unroll
-        for (int ab = 0; ab < NAB; ++ab) H[ab * NF + f] = y[ab];
-      }
-    }
-    __syncwarp();
-    {
-      const R CD[3] = {(R)ket.AB[0], (R)ket.AB[1], (R)ket.AB[2]};
-      for (int ab = lane; ab < NAB; ab += 32) {
-        R x[NF], y[NCD];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) x[f] = H[ab * NF + f];
-        C::template hrr_ket_row<R>(x, y, CD);
-        if constexpr (kPre) {
-          // FP64 and df64: stored once as a double, already multiplied by the
-          // d-component scales s_a s_b s_c s_d that every contraction needs
-          const double sab = comp_scale_rt(C::LA, ab / NB) * comp_scale_rt(C::LB, ab % NB);
-#pragma unroll
-          for (int cd = 0; cd < NCD; ++cd)
-            Id[ab * NCD + cd] = (double)y[cd] * (sab * comp_scale_rt(C::LC, cd / ND) * comp_scale_rt(C::LD, cd % ND));
-        } else {
-#pragma unroll
-          for (int cd = 0; cd < NCD; ++cd) I[ab * NCD + cd] = y[cd];
-        }
-      }
-    }
     __syncwarp();
     // digestion: one output element per lane for each of the six contractions
     const MolJK& mo = mjp ? *mjp : one;
@@ -738,32 +819,37 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
     if (ket.same) wdeg *= 0.5;
     if (bp == kp) wdeg *= 0.5;
     const int a0 = bra.bfA, b0 = bra.bfB, c0 = ket.bfA, d0 = ket.bfB;
-    auto Dsc_of = [&](const double* __restrict__ Dm, int r0, int lr, int i, int c0_, int lc, int j) {
-      const double dv = __ldg(Dm + (size_t)(r0 + i) * nbf + c0_ + j);
+    // digestion arithmetic: FP32 for the reduced-precision quartets, FP64
+    // otherwise; every sum is added into the FP64 J and K
+    using Dg = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
+    auto Dsc_of = [&](const double* __restrict__ Dm, int r0, int lr, int i, int c0_, int lc, int j) -> Dg {
+      const Dg dv = (Dg)__ldg(Dm + (size_t)(r0 + i) * nbf + c0_ + j);
       if constexpr (kPre) return dv;
-      else return dv * comp_scale_rt(lr, i) * comp_scale_rt(lc, j);
+      else return dv * (Dg)comp_scale_rt(lr, i) * (Dg)comp_scale_rt(lc, j);
     };
     auto Dsc = [&](int r0, int lr, int i, int c0_, int lc, int j) { return Dsc_of(Dj, r0, lr, i, c0_, lc, j); };
-    auto Iv = [&](int a, int b, int c, int d) {
+    auto Iv = [&](int a, int b, int c, int d) -> Dg {
       if constexpr (kPre) return Id[((a * NB + b) * NC + c) * ND + d];
-      else return (double)I[((a * NB + b) * NC + c) * ND + d];
+      else return (Dg)I[((a * NB + b) * NC + c) * ND + d];
     };
     // scale of an output element: in the pre-scaled forms all four
     // component scales are already inside the integrals
-    auto osc = [&](int l1, int i, int l2, int j) { return kPre ? 1.0 : comp_scale_rt(l1, i) * comp_scale_rt(l2, j); };
+    auto osc = [&](int l1, int i, int l2, int j) -> Dg {
+      return kPre ? (Dg)1 : (Dg)comp_scale_rt(l1, i) * (Dg)comp_scale_rt(l2, j);
+    };
     for (int o = lane; o < NAB; o += 32) {  // J'_ab = w sum_cd I D_cd
       const int a = o / NB, b = o % NB;
-      double acc2 = 0.0;
+      Dg acc2 = (Dg)0;
       for (int c = 0; c < NC; ++c)
         for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsc(c0, C::LC, c, d0, C::LD, d), acc2);
-      atomicAdd(J + (size_t)(a0 + a) * nbf + b0 + b, acc2 * wdeg * osc(C::LA, a, C::LB, b));
+      jk_acc(J, (size_t)(a0 + a) * nbf + b0 + b, (double)(acc2 * (Dg)wdeg * osc(C::LA, a, C::LB, b)), kc.det);
     }
     for (int o = lane; o < NCD; o += 32) {  // J'_cd = w sum_ab I D_ab
       const int c = o / ND, d = o % ND;
-      double acc2 = 0.0;
+      Dg acc2 = (Dg)0;
       for (int a = 0; a < C::NA; ++a)
         for (int b = 0; b < NB; ++b) acc2 = fma(Iv(a, b, c, d), Dsc(a0, C::LA, a, b0, C::LB, b), acc2);
-      atomicAdd(J + (size_t)(c0 + c) * nbf + d0 + d, acc2 * wdeg * osc(C::LC, c, C::LD, d));
+      jk_acc(J, (size_t)(c0 + c) * nbf + d0 + d, (double)(acc2 * (Dg)wdeg * osc(C::LC, c, C::LD, d)), kc.det);
     }
 #pragma unroll 1
     for (int sp = 0; sp < nspin; ++sp) {  // exchange of each spin: K from D, K2 from D2
@@ -772,35 +858,63 @@ __global__ void __launch_bounds__(128) eri_jk_coop_kernel(const JKWork w, const 
     auto Dsk = [&](int r0, int lr, int i, int c0_, int lc, int j) { return Dsc_of(Dk, r0, lr, i, c0_, lc, j); };
     for (int o = lane; o < C::NA * NC; o += 32) {  // K'_ac = w sum_bd I D_bd
       const int a = o / NC, c = o % NC;
-      double acc2 = 0.0;
+      Dg acc2 = (Dg)0;
       for (int b = 0; b < NB; ++b)
         for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsk(b0, C::LB, b, d0, C::LD, d), acc2);
-      atomicAdd(Kx + (size_t)(a0 + a) * nbf + c0 + c, acc2 * wdeg * osc(C::LA, a, C::LC, c));
+      jk_acc(Kx, (size_t)(a0 + a) * nbf + c0 + c, (double)(acc2 * (Dg)wdeg * osc(C::LA, a, C::LC, c)), kc.det);
     }
     for (int o = lane; o < C::NA * ND; o += 32) {  // K'_ad = w sum_bc I D_bc
       const int a = o / ND, d = o % ND;
-      double acc2 = 0.0;
+      Dg acc2 = (Dg)0;
       for (int b = 0; b < NB; ++b)
         for (int c = 0; c < NC; ++c) acc2 = fma(Iv(a, b, c, d), Dsk(b0, C::LB, b, c0, C::LC, c), acc2);
-      atomicAdd(Kx + (size_t)(a0 + a) * nbf + d0 + d, acc2 * wdeg * osc(C::LA, a, C::LD, d));
+      jk_acc(Kx, (size_t)(a0 + a) * nbf + d0 + d, (double)(acc2 * (Dg)wdeg * osc(C::LA, a, C::LD, d)), kc.det);
     }
     for (int o = lane; o < NB * NC; o += 32) {  // K'_bc = w sum_ad I D_ad
       const int b = o / NC, c = o % NC;
-      double acc2 = 0.0;
+      Dg acc2 = (Dg)0;
       for (int a = 0; a < C::NA; ++a)
         for (int d = 0; d < ND; ++d) acc2 = fma(Iv(a, b, c, d), Dsk(a0, C::LA, a, d0, C::LD, d), acc2);
-      atomicAdd(Kx + (size_t)(b0 + b) * nbf + c0 + c, acc2 * wdeg * osc(C::LB, b, C::LC, c));
+      jk_acc(Kx, (size_t)(b0 + b) * nbf + c0 + c, (double)(acc2 * (Dg)wdeg * osc(C::LB, b, C::LC, c)), kc.det);
     }
     for (int o = lane; o < NB * ND; o += 32) {  // K'_bd = w sum_ac I D_ac
       const int b = o / ND, d = o % ND;
-      double acc2 = 0.0;
+      Dg acc2 = (Dg)0;
       for (int a = 0; a < C::NA; ++a)
         for (int c = 0; c < NC; ++c) acc2 = fma(Iv(a, b, c, d), Dsk(a0, C::LA, a, c0, C::LC, c), acc2);
-      atomicAdd(Kx + (size_t)(b0 + b) * nbf + d0 + d, acc2 * wdeg * osc(C::LB, b, C::LD, d));
+      jk_acc(Kx, (size_t)(b0 + b) * nbf + d0 + d, (double)(acc2 * (Dg)wdeg * osc(C::LB, b, C::LD, d)), kc.det);
     }
     }  // spin
     __syncwarp();
   }
+}
+
+// Q_ab of the pairs of a warp-cooperative diagonal class (X|X): one warp per
+// pair evaluates (ab|ab) by coop_block and takes sqrt(max |(ab|ab)|) over
+// the Cartesian components (the thread-per-pair kernel below would hold
+// the whole [e0|f0] set of these classes in registers).
+template <class C>
+__global__ void __launch_bounds__(128) eri_schwarz_coop_kernel(const int* __restrict__ pairs, int npairs,
+                                                               const PairSet ps, const KernelCommon kc,
+                                                               double* __restrict__ Q, const int G) {
+  using S = CoopSizes<C>;
+  constexpr int NT = S::NT, NAB = S::NAB, NCD = S::NCD, NF = C::NF;
+  static_assert(NAB == NCD, "diagonal class");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* const s = reinterpret_cast<double*>(smem_raw) + (threadIdx.x >> 5) * S::ws(G);
+  const int lane = threadIdx.x & 31;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // one pair per warp
+  if (t >= npairs) return;
+  const int pid = pairs[t];
+  const PairInfo pr = ps.info[pid];
+  coop_block<C, double>(ps.prim64, kc, pr, pr, 0, pr.nprim * pr.nprim, s, G, lane);
+  __syncwarp();
+  const double* const Id = s + NT + NAB * NF;  // pre-scaled: (ab|ab) s_a^2 s_b^2
+  double m = 0.0;
+  for (int ab = lane; ab < NAB; ab += 32) m = fmax(m, fabs(Id[ab * NCD + ab]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) Q[pid] = sqrt(m);
 }
 
 // Primitive quartets set up per pass: the class default, or HF_COOP_G
@@ -833,6 +947,19 @@ inline void coop_launch(const JKWork& w, const PairSet& ps, const KernelCommon& 
   // shared memory per warp of the block (the attribute covers four warps)
   const size_t used = sm / 4 * (size_t)(threads / 32);
   eri_jk_coop_kernel<C, R><<<grid, threads, used, s>>>(w, ps, kc, one, mols, g);
+}
+
+template <class C>
+inline void schwarz_coop_launch(const int* pairs, int npairs, const PairSet& ps, const KernelCommon& kc, double* Q,
+                                cudaStream_t s) {
+  const int g = coop_group<C>();
+  const size_t sm = coop_smem_bytes<C, double>(g);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(eri_schwarz_coop_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  eri_schwarz_coop_kernel<C><<<(npairs + 3) / 4, 128, sm, s>>>(pairs, npairs, ps, kc, Q, g);
 }
 
 template <class C, typename R>
@@ -983,7 +1110,10 @@ __global__ void __launch_bounds__(128) eri_schwarz_kernel(const int* __restrict_
   }                                                                                                      \
   static void launch_schwarz_##CLS(const int* pairs, int npairs, const PairSet& ps, const KernelCommon& kc, \
                                    double* Q, cudaStream_t s) {                                          \
-    if (npairs > 0)                                                                                      \
+    if (npairs <= 0) return;                                                                             \
+    if constexpr (hfgen::CLS::COOP && hfgen::CLS::LA == hfgen::CLS::LC && hfgen::CLS::LB == hfgen::CLS::LD)  \
+      hfk::schwarz_coop_launch<hfgen::CLS>(pairs, npairs, ps, kc, Q, s);                                  \
+    else                                                                                                 \
       hfk::eri_schwarz_kernel<hfgen::CLS><<<(npairs + 127) / 128, 128, 0, s>>>(pairs, npairs, ps, kc, Q); \
   }                                                                                                      \
   static int occ_jk64_##CLS() { return occR_##CLS<double>(); }                                          \

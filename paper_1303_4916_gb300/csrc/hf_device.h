@@ -54,6 +54,8 @@ struct PairSet {
   const float* prim32;
   const PairInfo* info;
   const float* primdf;
+  int npairs;      // shell pairs (records of info)
+  int nprimpairs;  // primitive-pair records
 };
 
 #define HF_NPAIRCLASS 6
@@ -85,7 +87,28 @@ struct KernelCommon {
   int boys_fp32;  // evaluate F_m in FP32 for reduced-precision quartets
   const float* boysdf;
   int boys_df;    // reduced-precision quartets take F_m from the df64 evaluation (df64 tier)
+  int det;        // J/K outputs are fixed-point integer accumulators (deterministic order)
+  int* status;    // bounds-checked builds: first failed check (code, then the index), else unused
 };
+
+// Bounds-checked build (-DHF_BOUNDS_CHECK, small cases in place of a memory
+// checker): the J/K kernels test every work-item, pair, primitive-record,
+// Boys-row and matrix index before use; a failure stores its check code and
+// the offending index in kc.status (first failure wins) and skips the
+// access.  The host reads the status after each J/K build.  Without the
+// macro the checks compile to nothing.
+#ifdef HF_BOUNDS_CHECK
+#define HF_BCHECK(kc, ok, code, idx)                                   \
+  ((ok) ? true                                                          \
+        : (atomicCAS((kc).status, 0, (code)) == 0 ? (void)atomicExch((kc).status + 1, (int)(idx)) : (void)0, false))
+#else
+#define HF_BCHECK(kc, ok, code, idx) true
+#endif
+#define HF_BC_ITEM 1   // work-item entry or ket position
+#define HF_BC_PAIR 2   // shell-pair id
+#define HF_BC_PRIM 3   // primitive-pair record
+#define HF_BC_MAT 4    // D/J/K element
+#define HF_BC_BOYS 5   // Boys table row
 
 // Work list of one (class, precision) launch.  Entry e pairs bra pair
 // bra[e] with the kets ket[kbeg[e] .. kend[e]) of the ket class list

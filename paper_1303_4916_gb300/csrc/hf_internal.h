@@ -4,7 +4,10 @@
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
+#include <cstdio>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -45,11 +48,47 @@ struct hf_ctx {
   std::atomic<int> fail_countdown{0};
   std::atomic<long long> device_bytes{0};
   std::mutex mu;  // serialises use of the stream-bound library handles
+  int* bounds = nullptr;  // device status words of the bounds-checked build (2 ints)
+  // bases and servers created on this context and not yet destroyed;
+  // hf_ctx_destroy with live ones only marks the context, and the last
+  // hf_basis_destroy / hf_serve_destroy tears it down (they free their
+  // device memory through the context)
+  std::atomic<int> live_bases{0};
+  std::atomic<bool> destroy_pending{false};
+  // JSON-lines log of SCF iterations (hf_ctx_set_log); null = off
+  FILE* log = nullptr;
+  bool own_log = false;
+  std::mutex log_mu;
 };
+
+// NVTX range for the lifetime of a scope (a no-op unless a profiler is
+// attached): J/K builds, class launches, SCF iterations.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Bounds-checked builds: the first failed index check since the last call
+// (HF_ERR_INVALID with its code and index), else HF_OK; clears the status.
+// Always HF_OK in the normal build.
+int hf_bounds_status(hf_ctx* ctx, const char* where);
+
+// One JSON line per SCF iteration into the context's log (when set):
+// solver ("rhf", "uhf", "batch", "serve"), molecule tag, nbf, iteration,
+// energy, |dE| (null on the first iteration), max DIIS error, seconds since
+// the solve started, converged flag.
+void hf_log_scf_iter(hf_ctx* ctx, const char* solver, unsigned long long mol, int nbf, int iter, double energy,
+                     double delta_e, double diis_error, double t, int converged);
+// One ready-made JSON object (no newline) into the context's log, when set.
+void hf_log_line(hf_ctx* ctx, const char* json);
 
 // Stream-ordered device allocation through the context (honours the
 // fault-injection hook).  Returns HF_OK / HF_ERR_OOM.
 int hf_dev_alloc(hf_ctx* ctx, void** p, size_t bytes);
+// The teardown of hf_ctx_destroy (called when no basis is left).
+void hf_ctx_teardown(hf_ctx* ctx);
 void hf_dev_free(hf_ctx* ctx, void* p, size_t bytes);
 
 template <typename T>
@@ -118,6 +157,9 @@ struct hf_basis {
   DevArray<double> hD, hJ, hK;
   // D^a + D^b of an unrestricted J/K call
   DevArray<double> Dsum;
+  // fixed-point J', K' (and K2') accumulators of HF_JK_DETERMINISTIC builds,
+  // two 64-bit words per element
+  DevArray<unsigned long long> detq;
 
   // one-electron data (lazily)
   DevArray<double> S, T, V;
@@ -127,7 +169,7 @@ struct hf_basis {
 int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound);
 
 inline PairSet hf_pairset(const hf_basis* b) {
-  return PairSet{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr, b->primdf.ptr};
+  return PairSet{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr, b->primdf.ptr, b->npairs, b->nprimpairs};
 }
 // Boys function of the reduced-precision (FP32) quartets: FP32 with
 // HF_JK_FP32_BOYS; else df64 in the df64 tier (the tier's stand-in for FP64);
@@ -135,7 +177,14 @@ inline PairSet hf_pairset(const hf_basis* b) {
 inline KernelCommon hf_kernel_common(const hf_ctx* c, unsigned jk_flags) {
   const int f32 = (jk_flags & HF_JK_FP32_BOYS) ? 1 : 0;
   const int df = (!f32 && (jk_flags & HF_JK_DF64)) ? 1 : 0;
-  return KernelCommon{c->boys64, c->boys32, f32, c->boysdf, df};
+  return KernelCommon{c->boys64, c->boys32, f32, c->boysdf, df, 0, c->bounds};  // det: set by hf_jk_run only
+}
+// HF_JK_DETERMINISTIC is served by hf_fock_jk, hf_fock_jk_profiled and
+// hf_fock_jk_uhf; the entry points that build J/K elsewhere reject it.
+inline int hf_reject_deterministic(unsigned jk_flags, const char* who) {
+  return (jk_flags & HF_JK_DETERMINISTIC)
+             ? hf_fail(HF_ERR_INVALID, "%s: HF_JK_DETERMINISTIC is served by hf_fock_jk and hf_fock_jk_uhf only", who)
+             : HF_OK;
 }
 // launcher for the higher-precision work of a class: df64 when requested
 inline jk_launch_fn hf_jk_hi(const EriClassOps& op, unsigned jk_flags) {

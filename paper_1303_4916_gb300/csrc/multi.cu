@@ -1,5 +1,7 @@
 // multi.cu -- multi-molecule J/K launches (batched SCF and serving).
 #include <algorithm>
+#include <cstdio>
+#include <string>
 
 #include "multi.h"
 
@@ -145,6 +147,7 @@ int MultiJK::set_active(const std::vector<int>& active) {
 }
 
 int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
+  NvtxRange nv_build("multi-molecule J/K build");
   cudaStream_t st = ctx->stream;
   if (nmol == 0) return HF_OK;
   const dim3 g(std::max(1, 2 * ctx->num_sms / std::max(1, nmol)), nmol);
@@ -177,6 +180,7 @@ int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
       const int occ = std::max(r == 0 ? hf_occ_hi(op, jk_flags) : op.occ32(), 1);
       const LaunchShape sh = hf_launch_shape(ctx, occ, wk.nitems, grid_scale[cls]);
       cudaStream_t ls = fork ? ctx->side[nlaunch++ % hf_ctx::kSide] : st;
+      NvtxRange nv_cls(op.name);
       (r == 0 ? hf_jk_hi(op, jk_flags) : op.jk32)(wk, none, kc, one, table.ptr, sh.grid, sh.threads, ls);
     }
     if (class_ms && any) {
@@ -200,6 +204,7 @@ int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
   }
   symmetrize_jk_batch<<<g, 256, 0, st>>>(table.ptr);
   HF_CUDA(cudaGetLastError());
+  if (!capturing) HF_CHECK(hf_bounds_status(ctx, "multi-molecule J/K build"));
   return HF_OK;
 }
 
@@ -215,6 +220,20 @@ int MultiJK::tune_step(const KernelCommon& kc) {
       grid_scale[c] = cand[best];
     }
     tuned = true;
+    // the choices, with the trial times, into the context's log
+    std::string js = "{\"event\": \"autotune\", \"molecules\": " + std::to_string(nmol) + ", \"classes\": [";
+    bool first = true;
+    for (int c = 0; c < HF_NCLASS; ++c) {
+      if (tune_ms[0][c] <= 0.0) continue;
+      char buf[256];
+      snprintf(buf, sizeof buf,
+               "%s{\"class\": \"%s\", \"blocks_per_sm\": %d, \"ms_full\": %.4f, \"ms_2\": %.4f, \"ms_1\": %.4f}",
+               first ? "" : ", ", ctx->ops[c].name, grid_scale[c], tune_ms[0][c], tune_ms[1][c], tune_ms[2][c]);
+      js += buf;
+      first = false;
+    }
+    js += "]}";
+    hf_log_line(ctx, js.c_str());
   }
   return HF_OK;
 }
@@ -236,7 +255,9 @@ int MultiJK::capture(const KernelCommon& kc) {
     ctx->ops[c].occdf();
   }
   HF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  capturing = true;
   const int rc = launch(kc);
+  capturing = false;
   cudaGraph_t gph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(st, &gph);
   if (rc != HF_OK) {
@@ -252,6 +273,7 @@ int MultiJK::capture(const KernelCommon& kc) {
 int MultiJK::run(const KernelCommon& kc) {
   if (!graph_exec) return launch(kc);
   HF_CUDA(cudaGraphLaunch(graph_exec, ctx->stream));
+  HF_CHECK(hf_bounds_status(ctx, "multi-molecule J/K build"));
   return HF_OK;
 }
 

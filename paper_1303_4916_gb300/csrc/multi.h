@@ -50,5 +50,6 @@ struct MultiJK {
   int run(const KernelCommon& kc);
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  bool capturing = false;  // inside capture(): no host reads of device status
   ~MultiJK();
 };

@@ -66,6 +66,7 @@ extern "C" int hf_fock_jk_noalloc(hf_basis* b, const double* D, double* J, doubl
   if (!(o.schwarz_tau >= 0.0) || !(o.fp32_bound >= 0.0)) return hf_fail(HF_ERR_INVALID, "negative threshold");
   if (o.flags & HF_JK_HOST)
     return hf_fail(HF_ERR_INVALID, "hf_fock_jk_noalloc: device pointers only (HF_JK_HOST needs staging buffers)");
+  HF_CHECK(hf_reject_deterministic(o.flags, "hf_fock_jk_noalloc"));
   const int n = b->nbf;
   if (n > HF_NOALLOC_MAX_NBF)
     return hf_fail(HF_ERR_TOO_LARGE, "hf_fock_jk_noalloc: nbf %d exceeds the static scratch limit of %d", n,

@@ -15,6 +15,7 @@
 // Matrices are symmetric except C and the DIIS products; cuBLAS works
 // column-major, so a row-major symmetric buffer is read as itself.
 #include <algorithm>
+#include <cstdint>
 #include <chrono>
 #include <cstring>
 #include <cmath>
@@ -464,6 +465,7 @@ extern "C" int hf_scf_solve(hf_basis* b, const hf_scf_opts* opts, hf_scf_result*
   hf_scf_opts_default(&o);
   if (opts) o = *opts;
   if (o.max_iter < 1 || o.diis_size < 0 || !(o.e_tol >= 0.0)) return hf_fail(HF_ERR_INVALID, "bad SCF options");
+  HF_CHECK(hf_reject_deterministic(o.jk.flags, "hf_scf_solve"));
   hf_ctx* ctx = b->ctx;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
@@ -488,6 +490,7 @@ extern "C" int hf_scf_solve(hf_basis* b, const hf_scf_opts* opts, hf_scf_result*
     HF_CHECK(mj.capture(kc));
   }
   for (;;) {
+    NvtxRange nv("scf iteration (rhf)");
     if (G.ptr) {
       HF_CHECK(scf_iterate(b, s, o, G.ptr));
     } else {
@@ -498,7 +501,10 @@ extern "C" int hf_scf_solve(hf_basis* b, const hf_scf_opts* opts, hf_scf_result*
       HF_CUDA(cudaStreamSynchronize(ctx->stream));
       HF_CHECK(scf_diis_step(b, s));
     }
-    if (scf_after_iter(b, s, o)) break;
+    const bool done = scf_after_iter(b, s, o);
+    hf_log_scf_iter(ctx, "rhf", (unsigned long long)(uintptr_t)b, b->nbf, s.iter, s.energy, s.delta_e, s.diis_error,
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), s.converged);
+    if (done) break;
   }
   HF_CHECK(scf_finish(b, s, res));
   res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -637,6 +643,7 @@ extern "C" int hf_uhf_solve(hf_basis* b, int n_alpha, int n_beta, const hf_scf_o
       (o.jk.flags & HF_JK_HOST))
     return hf_fail(HF_ERR_INVALID, "hf_uhf_solve: bad options (direct J/K, core guess, device buffers)");
   if (!(o.jk.schwarz_tau >= 0.0) || !(o.jk.fp32_bound >= 0.0)) return hf_fail(HF_ERR_INVALID, "negative threshold");
+  HF_CHECK(hf_reject_deterministic(o.jk.flags, "hf_uhf_solve"));
   hf_ctx* ctx = b->ctx;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
@@ -661,6 +668,7 @@ extern "C" int hf_uhf_solve(hf_basis* b, int n_alpha, int n_beta, const hf_scf_o
   s.e_old = NAN;
   s.delta_e = NAN;
   for (;;) {
+    NvtxRange nv("scf iteration (uhf)");
     HF_CHECK(uhf_density(b, u, nocc));
     HF_CHECK(mj.run(kc));
     s.quartets += mj.mol_quartets[0];
@@ -679,6 +687,8 @@ extern "C" int hf_uhf_solve(hf_basis* b, int n_alpha, int n_beta, const hf_scf_o
       }
     }
     s.e_old = s.energy;
+    hf_log_scf_iter(ctx, "uhf", (unsigned long long)(uintptr_t)b, b->nbf, s.iter, s.energy, s.delta_e, s.diis_error,
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), s.converged);
     if (done || s.iter >= o.max_iter) break;
   }
   double s2 = 0.0;

@@ -166,6 +166,7 @@ void hf_server::run() {
       membership_changed = false;
     }
     // one SCF iteration for every active molecule
+    NvtxRange nv("serve round");
     for (Request* r : active)
       if (rc == HF_OK) rc = scf_density(r->basis, *r->scf);
     if (rc == HF_OK && !tuned) {
@@ -194,7 +195,10 @@ void hf_server::run() {
         finished.push_back({r, rr});
         continue;
       }
-      if (scf_after_iter(r->basis, *r->scf, opts.scf)) {
+      const bool done = scf_after_iter(r->basis, *r->scf, opts.scf);
+      hf_log_scf_iter(ctx, "serve", (unsigned long long)r->ticket, r->basis->nbf, r->scf->iter, r->scf->energy,
+                      r->scf->delta_e, r->scf->diis_error, now() - r->result.t_admit, r->scf->converged);
+      if (done) {
         hf_scf_result res{};
         scf_finish(r->basis, *r->scf, &res);
         r->result.energy = res.energy;
@@ -234,12 +238,14 @@ extern "C" int hf_serve_create(hf_ctx* ctx, const hf_serve_opts* opts, hf_server
   if (o.max_active < 1 || o.queue_capacity < 1 || o.scf.max_iter < 1 || o.scf.diis_size < 0 ||
       (o.scf.flags & HF_SCF_STORED_ERI) || o.scf.D0)
     return hf_fail(HF_ERR_INVALID, "hf_serve_create: bad options");
+  HF_CHECK(hf_reject_deterministic(o.scf.jk.flags, "hf_serve_create"));
   hf_server* s = new (std::nothrow) hf_server();
   if (!s) return hf_fail(HF_ERR_OOM, "host allocation");
   s->ctx = ctx;
   s->opts = o;
   s->budget = o.hbm_budget ? o.hbm_budget : ctx->hbm_budget;
   s->t0 = std::chrono::steady_clock::now();
+  ctx->live_bases.fetch_add(1);
   s->worker = std::thread([s] { s->run(); });
   *out = s;
   return HF_OK;
@@ -336,5 +342,8 @@ extern "C" void hf_serve_destroy(hf_server* s) {
   for (auto& kv : s->reqs) {
     if (kv.second->basis) hf_basis_destroy(kv.second->basis);
   }
+  hf_ctx* ctx = s->ctx;
   delete s;
+  // a server keeps its context alive like a basis does
+  if (ctx->live_bases.fetch_sub(1) == 1 && ctx->destroy_pending.load()) hf_ctx_teardown(ctx);
 }

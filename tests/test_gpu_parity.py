@@ -316,3 +316,98 @@ def test_single_function_and_zero_electrons(ctx, hf):
     D = _density(b0.nbf, 1) * 0.0
     J, K = b0.fock_jk(_t(D))
     assert float(J.abs().max()) == 0.0 and float(K.abs().max()) == 0.0
+
+
+def test_deterministic_jk_is_bitwise_reproducible(ctx, hf):
+    """HF_JK_DETERMINISTIC: the fixed-point accumulation gives the same bits
+    on every call (FP64 atomics do not), matches the default build and the
+    oracle within the J/K tolerance, for RHF and unrestricted J/K, and every
+    precision tier."""
+    import torch
+    mol = lattice_molecule(6, 21, "spd")
+    basis = hf.Basis(ctx, mol)
+    ob = oracle.Basis(mol)
+    n = basis.nbf
+    rng = np.random.default_rng(5)
+    Cm = rng.normal(size=(n, 4)) / np.sqrt(n)
+    Dn = Cm @ Cm.T
+    Jr, Kr, _ = ob.jk(Dn, tau=1e-12, nthreads=oracle.oracle_threads())
+    D = torch.tensor(Dn, device="cuda:0")
+    for tier in ({}, {"df64": True}, {"fp32_bound": 1e-5, "df64": True}):
+        Jd, Kd = basis.fock_jk(D, opts=hf.jk_opts(deterministic=True, **tier))
+        for _ in range(3):
+            J2, K2 = basis.fock_jk(D, opts=hf.jk_opts(deterministic=True, **tier))
+            assert torch.equal(J2, Jd) and torch.equal(K2, Kd), tier
+        tol = JK_TOL if "fp32_bound" not in tier else 1e-7
+        assert np.abs(Jd.cpu().numpy() - Jr).max() <= tol and np.abs(Kd.cpu().numpy() - Kr).max() <= tol, tier
+    Db = D * 0.5
+    a = basis.fock_jk_uhf(D, Db, opts=hf.jk_opts(deterministic=True))
+    b = basis.fock_jk_uhf(D, Db, opts=hf.jk_opts(deterministic=True))
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    assert float((a[0] - torch.tensor(1.5 * Jr, device="cuda:0")).abs().max()) <= JK_TOL
+    import ctypes
+    from paper_1303_4916_gb300 import _abi
+    o = hf.hf_scf_opts_default()                         # the SCF does not take the flag
+    o.jk = hf.jk_opts(deterministic=True)
+    r = _abi.hf_scf_result()
+    assert hf.load().hf_scf_solve(basis.handle, ctypes.byref(o), ctypes.byref(r)) == _abi.HF_ERR_INVALID
+
+
+def test_scf_iteration_log(ctx, hf, tmp_path):
+    """hf_ctx_set_log: one JSON line per SCF iteration (RHF and UHF) with the
+    energy sequence the solve reports."""
+    import json
+    path = tmp_path / "scf.jsonl"
+    c = hf.Context(0)
+    c.set_log(str(path))
+    mol = lattice_molecule(3, 51, "sp")
+    b = hf.Basis(c, mol)
+    r = b.scf(max_iter=64, e_tol=1e-9, diis_size=8)
+    u = b.uhf(mol.n_electrons // 2 + 1, mol.n_electrons // 2 - 1, max_iter=64, e_tol=1e-9)
+    c.set_log(None)
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    rhf = [x for x in lines if x["solver"] == "rhf"]
+    uhf = [x for x in lines if x["solver"] == "uhf"]
+    assert len(rhf) == r.iterations and len(uhf) == u.iterations
+    assert [x["iter"] for x in rhf] == list(range(1, r.iterations + 1))
+    assert rhf[0]["delta_e"] is None and rhf[-1]["converged"] == int(r.converged)
+    assert abs(rhf[-1]["energy"] - r.energy) <= 1e-12 and abs(uhf[-1]["energy"] - u.energy) <= 1e-12
+    assert all(x["nbf"] == b.nbf and x["t"] >= 0.0 for x in lines)
+
+
+def test_context_outlived_by_its_bases(hf):
+    """A context destroyed while bases and a server made on it are alive
+    stays usable by them; the last of them completes the teardown (the order
+    a garbage collector may pick at interpreter exit)."""
+    import torch
+    lib = hf.load()
+    c = hf.Context(0)
+    mol = lattice_molecule(3, 51, "sp")
+    b1 = hf.Basis(c, mol)
+    b2 = hf.Basis(c, mol)
+    srv = hf.Server(c, max_active=2)
+    c.close()                                             # destroy pending: three users alive
+    D = torch.eye(b1.nbf, dtype=torch.float64, device="cuda:0") * 0.1
+    J, K = b1.fock_jk(D)
+    torch.cuda.synchronize()
+    assert torch.isfinite(J).all() and torch.isfinite(K).all()
+    b1.close()
+    srv.close()
+    e = b2.scf(max_iter=64).energy                       # still works
+    assert np.isfinite(e)
+    b2.close()                                            # the last user: teardown happens here
+    from paper_1303_4916_gb300 import _abi
+    assert lib.hf_strerror(_abi.HF_OK) is not None
+
+
+def test_scf_restart_from_density(ctx, hf):
+    """Checkpoint / resume: an SCF started from a converged density (D0)
+    lands on the same energy within two iterations."""
+    mol = lattice_molecule(6, 32, "sp")
+    b = hf.Basis(ctx, mol)
+    r = b.scf(max_iter=128, e_tol=1e-10, diis_size=8)
+    assert r.converged
+    r2 = b.scf(max_iter=128, e_tol=1e-10, diis_size=8, D0=r.tensors["D"])
+    assert r2.converged and r2.iterations <= 3
+    assert abs(r2.energy - r.energy) <= 1e-9
