@@ -959,6 +959,33 @@ def run_serve(args):
                       "config": {"workload": r["workload"]}, **r}), flush=True)
 
 
+def run_setup(args):
+    """Basis set-up (pair records, Schwarz factors, work lists) of the first
+    --nreq molecules of the serving stream (atoms log-uniform [4, --atoms-max],
+    s+p+d): the per-request admission cost of the server."""
+    import torch
+    import paper_1303_4916_gb300 as hf
+    from synth import lattice_molecule, serve_stream
+    t_arr, sizes, seeds = serve_stream(args.nreq, atoms=(4, args.atoms_max))
+    mols = [lattice_molecule(int(n), int(sd), "spd") for n, sd in zip(sizes, seeds)]
+    ctx = hf.Context(0)
+    hf.Basis(ctx, mols[0]).close()
+    torch.cuda.synchronize()
+    per = []
+    for m in mols:
+        t0 = time.perf_counter()
+        b = hf.Basis(ctx, m)
+        b.count_quartets(hf.jk_opts())
+        torch.cuda.synchronize()
+        per.append({"natom": int(m.natom), "nbf": int(b.nbf), "seconds": time.perf_counter() - t0})
+        b.close()
+    tot = sum(p["seconds"] for p in per)
+    print(json.dumps({"metric": "basis set-up", "unit": "s", "value": tot / len(per), "higher_is_better": False,
+                      "config": {"workload": f"first {len(mols)} requests of the serving stream, atoms "
+                                             f"logU[4,{args.atoms_max}], s+p+d"},
+                      "total_s": tot, "per_request": per}), flush=True)
+
+
 def run_classes(args):
     """Per-class kernel time and achieved FP64 rate on an s+p+d lattice
     molecule (--natom atoms, seed 3), one J/K build at a seeded density."""
@@ -999,7 +1026,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c3check", "batch", "serve", "classes"],
+    ap.add_argument("--workload", default="c2",
+                    choices=["c2", "c1", "c3", "c3check", "batch", "serve", "classes", "setup"],
                     help="c2 (default) is the benchmark line; the others print secondary measurements")
     ap.add_argument("--nmol", type=int, default=64)
     ap.add_argument("--nreq", type=int, default=24)
@@ -1025,7 +1053,7 @@ def main():
         return run_reference(args)
     if args.workload != "c2":
         return {"c1": run_c1, "c3": run_c3, "c3check": run_c3check, "batch": run_batch, "serve": run_serve,
-                "classes": run_classes}[args.workload](args)
+                "classes": run_classes, "setup": run_setup}[args.workload](args)
     return run_ours(args)
 
 
