@@ -60,7 +60,9 @@ extern "C" {
 #define HF_ERR_TOO_LARGE (-12)     /* request footprint exceeds the HBM budget, or a
                                       class's work list exceeds 2^30 items */
 
-#define HF_LMAX 2                  /* highest shell angular momentum (d) */
+#define HF_LMAX 4                  /* highest shell angular momentum (g); quartets with an f or
+                                      g shell take the Rys-quadrature route (Eq. 5 by Rys
+                                      quadrature, as the paper evaluates it) */
 #define HF_MAX_NPRIM 16            /* most primitives in one contracted shell */
 
 /* ---------------------------------------------------------------- types */
@@ -75,7 +77,7 @@ typedef struct {
     double xyz[3];
 } hf_atom;
 
-/* One contracted shell (Eq. 1): centre atom, angular momentum l (0..2),
+/* One contracted shell (Eq. 1): centre atom, angular momentum l (0..4),
  * nprim primitives starting at exps[prim_off], coefs[prim_off].  The
  * coefficients d_n multiply normalised primitives; the library rescales
  * the contraction to unit norm. */
@@ -99,6 +101,11 @@ typedef struct {
 #define HF_JK_DF64 8u              /* quartets above fp32_bound run in double-float (FP32-pair)
                                       arithmetic, ~1e-14 relative, in every class (J/K
                                       digestion and accumulation stay FP64) */
+#define HF_JK_RYS 16u              /* every class by Rys quadrature (Eq. 5, the paper's route) in
+                                      FP64, in place of the Obara-Saika / Head-Gordon-Pople
+                                      kernels of the s/p/d classes; classes with an f or g shell
+                                      always take it (in FP64 also under HF_JK_DF64 and for
+                                      quartets below fp32_bound) */
 typedef struct {
     double schwarz_tau;  /* drop shell quartet iff Q_ab*Q_cd < tau (default 1e-12; 0 keeps all) */
     double fp32_bound;   /* quartets with Q_ab*Q_cd < fp32_bound run in FP32 (default 0 = none) */
@@ -223,7 +230,7 @@ int hf_fock_jk(hf_basis* b, const double* D, double* J, double* K, const hf_jk_o
  * accounting: unique surviving shell quartets and primitive quartets
  * (after primitive-pair screening) in each precision, and the generated
  * operation counts of the class's recurrences. */
-#define HF_NCLASS 21
+#define HF_NCLASS 120             /* (la lb | lc ld) with l <= 4, pair classes ordered */
 typedef struct {
     int la, lb, lc, ld;
     int vrr_flops;           /* VRR operations per primitive quartet */
@@ -345,6 +352,19 @@ int hf_uhf_solve(hf_basis* b, int n_alpha, int n_beta, const hf_scf_opts* opts, 
  * n_occ in [1, nbf).  *e2 (host) receives E(2).  Errors: HF_ERR_INVALID,
  * HF_ERR_OOM, HF_ERR_CUDA. */
 int hf_mp2_energy(hf_basis* b, const double* C, const double* eps, int n_occ, double* e2);
+
+/* ---------------------------------------------------------------- Rys rule */
+
+/* The n-point Rys quadrature rule at T (Eq. 5 evaluated by Rys quadrature):
+ * roots u_i = t_i^2 (ascending) and weights w_i with
+ *   int_0^1 f(t^2) exp(-T t^2) dt = sum_i w_i f(u_i)
+ * exact for polynomials f of degree <= 2n - 1 (so sum_i w_i u_i^k = F_k(T),
+ * the Boys function, for k < 2n), from the same table the ERI kernels use
+ * (piecewise Chebyshev series for T < 60, the Gauss-Hermite limit above;
+ * about 1e-15 relative).  Host only, no device needed.  n in [1, 9];
+ * T finite and >= 0; u, w host arrays of n doubles.  Errors:
+ * HF_ERR_INVALID. */
+int hf_rys_rule(int n, double T, double* u, double* w);
 
 /* ---------------------------------------------------------------- batch */
 

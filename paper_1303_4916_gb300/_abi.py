@@ -27,13 +27,14 @@ HF_ERR_NOT_FOUND = -9
 HF_ERR_QUEUE_FULL = -10
 HF_ERR_CANCELLED = -11
 HF_ERR_TOO_LARGE = -12
-HF_LMAX = 2
+HF_LMAX = 4
 HF_MAX_NPRIM = 16
 
 HF_JK_HOST = 1
 HF_JK_DETERMINISTIC = 2
 HF_JK_FP32_BOYS = 4
 HF_JK_DF64 = 8
+HF_JK_RYS = 16
 HF_SCF_STORED_ERI = 1
 
 
@@ -79,7 +80,7 @@ class hf_class_stats(C.Structure):
                 ("quartets_fp32", C.c_longlong), ("prim_quartets_fp32", C.c_longlong)]
 
 
-HF_NCLASS = 21
+HF_NCLASS = 120
 
 
 class hf_serve_opts(C.Structure):
@@ -135,6 +136,7 @@ SIGNATURES = {
     "hf_fock_jk_uhf": (I, [P, P, P, P, P, P, C.POINTER(hf_jk_opts)]),
     "hf_uhf_solve": (I, [P, I, I, C.POINTER(hf_scf_opts), C.POINTER(hf_uhf_result)]),
     "hf_mp2_energy": (I, [P, P, P, I, C.POINTER(D)]),
+    "hf_rys_rule": (I, [I, D, C.POINTER(D), C.POINTER(D)]),
     "hf_scf_solve_batch": (I, [C.POINTER(P), I, C.POINTER(hf_scf_opts), C.POINTER(hf_scf_result),
                                C.POINTER(I)]),
     "hf_serve_opts_default": (None, [C.POINTER(hf_serve_opts)]),

@@ -59,8 +59,11 @@ def hf_scf_opts_default() -> hf_scf_opts:
 
 
 def jk_opts(schwarz_tau: Optional[float] = None, fp32_bound: Optional[float] = None, host: bool = False,
-            fp32_boys: bool = False, df64: bool = False, deterministic: bool = False) -> hf_jk_opts:
+            fp32_boys: bool = False, df64: bool = False, deterministic: bool = False,
+            rys: bool = False) -> hf_jk_opts:
     o = hf_jk_opts_default()
+    if rys:
+        o.flags |= _abi.HF_JK_RYS
     if deterministic:
         o.flags |= _abi.HF_JK_DETERMINISTIC
     if schwarz_tau is not None:
@@ -507,3 +510,13 @@ def hf_serve_cancel(server: Server, ticket: int) -> int:
 
 def hf_serve_drain(server: Server, timeout_s: float = 600.0):
     return server.drain(timeout_s)
+
+
+def hf_rys_rule(n: int, T: float):
+    """Roots u_i and weights w_i (numpy arrays) of the n-point Rys rule at T,
+    from the library's table (host only)."""
+    import numpy as np
+    u = (C.c_double * n)() if n > 0 else (C.c_double * 1)()
+    w = (C.c_double * n)() if n > 0 else (C.c_double * 1)()
+    _check(_lib().hf_rys_rule(int(n), float(T), u, w), "hf_rys_rule")
+    return np.array(u[:n]), np.array(w[:n])

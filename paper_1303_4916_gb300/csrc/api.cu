@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "hf_internal.h"
+#include "rys.cuh"
 
 static thread_local std::string g_last_error;
 
@@ -215,11 +216,22 @@ extern "C" int hf_ctx_create(hf_ctx** out, int device, size_t hbm_budget, void* 
     hf_register_classes_d4(c->ops);
     hf_register_classes_d5(c->ops);
     hf_register_classes_d6(c->ops);
+    hf_register_classes_rys(c->ops);
     for (int k = 0; k < HF_NCLASS; ++k)
       if (!c->ops[k].jk64) { rc = hf_fail(HF_ERR_CUDA, "class %d has no kernels", k); break; }
     if (rc != HF_OK) break;
     rc = hf_boys_tables(c);
     if (rc != HF_OK) break;
+    {
+      void* rp = nullptr;
+      rc = hf_dev_alloc(c, &rp, RYS_TAB_DOUBLES * sizeof(double));
+      if (rc != HF_OK) break;
+      c->rys = static_cast<double*>(rp);
+      if (cudaMemcpyAsync(c->rys, hf_rys_table_host(), RYS_TAB_DOUBLES * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream) != cudaSuccess)
+        rc = hf_fail(HF_ERR_CUDA, "Rys table upload");
+      if (rc != HF_OK) break;
+    }
     void* bp = nullptr;
     rc = hf_dev_alloc(c, &bp, 2 * sizeof(int));
     if (rc != HF_OK) break;
@@ -250,6 +262,7 @@ void hf_ctx_teardown(hf_ctx* c) {
   if (c->boys64) hf_dev_free(c, c->boys64, 0);
   if (c->boys32) hf_dev_free(c, c->boys32, 0);
   if (c->boysdf) hf_dev_free(c, c->boysdf, 0);
+  if (c->rys) hf_dev_free(c, c->rys, 0);
   if (c->bounds) hf_dev_free(c, c->bounds, 0);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (int k = 0; k < hf_ctx::kSide; ++k) {

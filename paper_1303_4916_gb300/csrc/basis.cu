@@ -420,8 +420,9 @@ extern "C" int hf_schwarz(hf_basis* b, double* Q) {
 // list positions <= the bra's own position are taken, so each unordered
 // pair of pairs appears once.  Kets with Q_i Q_k >= fp32_bound form the
 // FP64 range of the entry, the rest its FP32 range.
-int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
-  if (b->have_work && b->work_tau == tau && b->work_fp32 == fp32_bound) return HF_OK;
+int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound, unsigned flags) {
+  const bool rys = (flags & HF_JK_RYS) != 0;
+  if (b->have_work && b->work_tau == tau && b->work_fp32 == fp32_bound && b->work_rys == rys) return HF_OK;
   hf_ctx* ctx = b->ctx;
   cudaStream_t st = ctx->stream;
   for (int X = 0; X < HF_NPAIRCLASS; ++X)
@@ -430,7 +431,11 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
       const int xb = b->class_begin[X], xe = b->class_begin[X + 1];
       const int yb = b->class_begin[Y];
       const std::vector<int>& bk = b->buckets[Y];
-      const int chunk = ctx->ops[cls].chunk;
+      // Rys lists (f/g classes, or every class under HF_JK_RYS): one ket
+      // per item, each item split into the class's output chunks
+      const bool rys_list = rys || ctx->ops[cls].rys_native;
+      const int chunk = rys_list ? 1 : ctx->ops[cls].chunk;
+      const int nchunk = rys_list ? ctx->ops[cls].rys_nchunks : 0;
       std::vector<int> bra[2], kb[2], ke[2], io[2], sp[2];
       long long nq[2] = {0, 0};
       io[0].push_back(0);
@@ -470,7 +475,9 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
       // resident warp is below an item's length, the long items are cut
       // into parts of about that length: bra primitive pairs for the
       // thread-per-quartet kernels, primitive quartets (whole rounds of 32)
-      // for the warp-cooperative ones.  Large workloads are not split.
+      // for the warp-cooperative ones, any primitive-quartet range for the
+      // Rys kernel (whose items are further multiplied by its output
+      // chunks).  Large workloads are not split.
       const int yb_ = b->class_begin[Y];
       for (int r = 0; r < 2; ++r) {
         const size_t ne = bra[r].size();
@@ -480,17 +487,20 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
           const long long nbp = b->nprim_sig_h[bra[r][e]];
           const long long nkp = b->nprim_sig_h[b->ketlist_h[yb_ + kb[r][e]]];  // uniform inside a bucket
           len[e] = nbp * nkp;  // primitive quartets per lane (per warp for the cooperative kernels)
-          work += len[e] * ((ke[r][e] - kb[r][e] + chunk - 1) / chunk);
+          work += len[e] * ((ke[r][e] - kb[r][e] + chunk - 1) / chunk) * std::max(1, nchunk);
         }
         const long long warps = 16LL * ctx->num_sms;
-        const long long floor_len = chunk == 1 ? 64 : 16;
+        const long long floor_len = rys_list ? 16 : chunk == 1 ? 64 : 16;
         const long long target = std::max(floor_len, work / std::max(1LL, warps));
         sp[r].resize(ne);
         for (size_t e = 0; e < ne; ++e) {
           const long long nbp = b->nprim_sig_h[bra[r][e]];
           long long parts = (len[e] + target - 1) / target;
-          parts = std::min(parts, chunk == 1 ? std::max(1LL, (len[e] + 31) / 32) : std::max(1LL, nbp));
-          sp[r][e] = (int)std::max(1LL, parts);
+          parts = std::min(parts, rys_list ? std::max(1LL, len[e])
+                                           : chunk == 1 ? std::max(1LL, (len[e] + 31) / 32) : std::max(1LL, nbp));
+          parts = std::max(1LL, parts);
+          if (rys_list) parts = std::min(parts * nchunk, (long long)(1 << 20)) / nchunk * nchunk;
+          sp[r][e] = (int)parts;
           // item offsets are int on the device: checked in 64 bits, per entry
           const long long next =
               (long long)io[r].back() + (long long)((ke[r][e] - kb[r][e] + chunk - 1) / chunk) * sp[r][e];
@@ -524,6 +534,7 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
         w.w.nitems = io[r].back();
         w.w.counter = b->counters.ptr + 2 * cls + r;
         w.w.chunk = chunk;
+        w.w.nchunk = nchunk;
         w.nquartets = nq[r];
         w.bra_h = std::move(bra[r]);
         w.kbeg_h = std::move(kb[r]);
@@ -536,6 +547,7 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound) {
   b->have_work = true;
   b->work_tau = tau;
   b->work_fp32 = fp32_bound;
+  b->work_rys = rys;
   return HF_OK;
 }
 
@@ -546,7 +558,7 @@ extern "C" int hf_count_quartets(hf_basis* b, const hf_jk_opts* opts, long long*
   if (opts) o = *opts;
   std::lock_guard<std::mutex> lk(b->ctx->mu);
   cudaSetDevice(b->ctx->device);
-  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound));
+  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound, o.flags));
   long long t = 0, f = 0;
   for (int c = 0; c < HF_NCLASS; ++c) {
     t += b->work64[c].nquartets + b->work32[c].nquartets;
@@ -602,7 +614,12 @@ int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, d
     timing->n = 0;
     HF_CUDA(cudaEventRecord(timing->ev[timing->n++], st));
   }
-  // heaviest classes first
+  // heaviest classes first.  The f/g (Rys) classes are many and often
+  // small: without per-class timing they fork onto the side streams (round
+  // robin) and run beside each other and the s/p/d classes; every class
+  // shares only the J/K atomics with the others.
+  bool forked = false;
+  int nside = 0;
   for (int c = HF_NCLASS - 1; c >= 0; --c) {
     const EriClassOps& op = ctx->ops[c];
     for (int r = 0; r < 2; ++r) {
@@ -611,11 +628,20 @@ int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, d
       if (cw.w.nitems <= 0) continue;
       JKWork w = cw.w;
       w.counter = counters + 2 * c + r;
-      const jk_launch_fn fn = r == 0 ? hf_jk_hi(op, o.flags) : op.jk32;
-      const int occ = r == 0 ? hf_occ_hi(op, o.flags) : op.occ32();
+      const jk_launch_fn fn = r == 0 ? hf_jk_hi(op, o.flags) : hf_jk_lo(op, o.flags);
+      const int occ = r == 0 ? hf_occ_hi(op, o.flags) : hf_occ_lo(op, o.flags);
       const LaunchShape sh = hf_launch_shape(ctx, occ, w.nitems);
       NvtxRange nv_cls(op.name);
-      fn(w, ps, kc, one, nullptr, sh.grid, sh.threads, st);
+      cudaStream_t ls = st;
+      if (!timing && (op.rys_native || (o.flags & HF_JK_RYS))) {
+        if (!forked) {
+          HF_CUDA(cudaEventRecord(ctx->fork_ev, st));
+          for (int k = 0; k < hf_ctx::kSide; ++k) HF_CUDA(cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0));
+          forked = true;
+        }
+        ls = ctx->side[nside++ % hf_ctx::kSide];
+      }
+      fn(w, ps, kc, one, nullptr, sh.grid, sh.threads, ls);
       if (timing) {
         timing->which[timing->n - 1] = 2 * c + r;
         HF_CUDA(cudaEventRecord(timing->ev[timing->n++], st));
@@ -623,6 +649,11 @@ int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, d
     }
   }
   HF_CUDA(cudaGetLastError());
+  if (forked)
+    for (int k = 0; k < hf_ctx::kSide; ++k) {
+      HF_CUDA(cudaEventRecord(ctx->join_ev[k], ctx->side[k]));
+      HF_CUDA(cudaStreamWaitEvent(st, ctx->join_ev[k], 0));
+    }
   double* K2 = spin ? spin->K2 : nullptr;
   if (det)
     finish_fixed<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(q, q + 2 * nn, spin ? q + 4 * nn : nullptr, J, K, K2,
@@ -638,7 +669,7 @@ int hf_jk_run(hf_basis* b, const double* D, double* Jp, double* Kp, double* J, d
 int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts& o, long long* nq) {
   hf_ctx* ctx = b->ctx;
   cudaStream_t st = ctx->stream;
-  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound));
+  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound, o.flags));
   const size_t nn = (size_t)b->nbf * b->nbf;
   HF_CUDA(cudaMemsetAsync(J, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(K, 0, nn * sizeof(double), st));
@@ -662,7 +693,7 @@ extern "C" int hf_class_stats_get(hf_basis* b, const hf_jk_opts* opts, hf_class_
   if (opts) o = *opts;
   std::lock_guard<std::mutex> lk(b->ctx->mu);
   cudaSetDevice(b->ctx->device);
-  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound));
+  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound, o.flags));
   // prefix sums of significant primitive-pair counts along each class's ket list
   std::vector<long long> pre(b->npairs + 1, 0);
   for (int k = 0; k < b->npairs; ++k) pre[k + 1] = pre[k] + b->nprim_sig_h[b->ketlist_h[k]];
@@ -670,13 +701,14 @@ extern "C" int hf_class_stats_get(hf_basis* b, const hf_jk_opts* opts, hf_class_
     for (int Y = 0; Y <= X; ++Y) {
       const int c = X * (X + 1) / 2 + Y;
       hf_class_stats& st = out[c];
-      static const int lx[6] = {0, 1, 1, 2, 2, 2}, ly[6] = {0, 0, 1, 0, 1, 2};
-      st.la = lx[X]; st.lb = ly[X]; st.lc = lx[Y]; st.ld = ly[Y];
+      pair_ls(X, &st.la, &st.lb);
+      pair_ls(Y, &st.lc, &st.ld);
       const EriClassOps& op = b->ctx->ops[c];
       const int L = st.la + st.lb + st.lc + st.ld;
       st.vrr_flops = op.vrr_flops;
       st.hrr_flops = op.hrr_flops;
-      st.prim_flops = op.vrr_flops + prim_overhead_flops(L);
+      // the Rys classes' count already holds their set-up and quadrature rule
+      st.prim_flops = op.vrr_flops + (op.jk64 == op.jkrys ? 0 : prim_overhead_flops(L));
       const int nblk = ((st.la + 1) * (st.la + 2) / 2) * ((st.lb + 1) * (st.lb + 2) / 2) *
                        ((st.lc + 1) * (st.lc + 2) / 2) * ((st.ld + 1) * (st.ld + 2) / 2);
       st.digest_flops = 6 * 2 * nblk;
@@ -707,7 +739,7 @@ extern "C" int hf_fock_jk_profiled(hf_basis* b, const double* D, double* J, doub
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
   cudaStream_t st = ctx->stream;
-  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound));
+  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound, o.flags));
   const size_t nn = (size_t)b->nbf * b->nbf;
   HF_CUDA(cudaMemsetAsync(J, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(K, 0, nn * sizeof(double), st));
@@ -766,7 +798,7 @@ int hf_fock_jk_uhf_device(hf_basis* b, const double* Da, const double* Db, const
                           double* Kb, const hf_jk_opts& o, long long* nq) {
   hf_ctx* ctx = b->ctx;
   cudaStream_t st = ctx->stream;
-  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound));
+  HF_CHECK(hf_basis_prepare_work(b, o.schwarz_tau, o.fp32_bound, o.flags));
   const size_t nn = (size_t)b->nbf * b->nbf;
   HF_CUDA(cudaMemsetAsync(J, 0, nn * sizeof(double), st));
   HF_CUDA(cudaMemsetAsync(Ka, 0, nn * sizeof(double), st));
@@ -812,7 +844,7 @@ extern "C" int hf_eri_tensor(hf_basis* b, double* G) {
 int hf_eri_tensor_device(hf_basis* b, double* G) {
   hf_ctx* ctx = b->ctx;
   cudaStream_t st = ctx->stream;
-  HF_CHECK(hf_basis_prepare_work(b, 0.0, 0.0));
+  HF_CHECK(hf_basis_prepare_work(b, 0.0, 0.0, 0u));
   HF_CUDA(cudaMemsetAsync(b->counters.ptr, 0, sizeof(int) * 2 * HF_NCLASS, st));
   const PairSet ps = hf_pairset(b);
   const KernelCommon kc = hf_kernel_common(ctx, 0);

@@ -45,7 +45,7 @@ extern "C" int hf_scf_solve_batch(hf_basis* const* bases, int count, const hf_sc
   int first_error = HF_OK;
   for (int i = 0; i < count; ++i) {
     S[i].reset(new ScfState());
-    int rc = hf_basis_prepare_work(mols[i], o.jk.schwarz_tau, o.jk.fp32_bound);
+    int rc = hf_basis_prepare_work(mols[i], o.jk.schwarz_tau, o.jk.fp32_bound, o.jk.flags);
     if (rc == HF_OK) rc = scf_state_init(mols[i], *S[i], o.diis_size);
     if (rc == HF_OK) rc = scf_begin(mols[i], *S[i], o, nullptr);
     status[i] = rc;

@@ -58,7 +58,7 @@ struct PairSet {
   int nprimpairs;  // primitive-pair records
 };
 
-#define HF_NPAIRCLASS 6
+#define HF_NPAIRCLASS 15  // (la, lb), la >= lb, l <= 4
 
 // One molecule of a launch: density and J/K outputs (device, nbf x nbf
 // row-major), its own pair data and ket lists (ket_off[Y] = start of pair
@@ -89,6 +89,7 @@ struct KernelCommon {
   int boys_df;    // reduced-precision quartets take F_m from the df64 evaluation (df64 tier)
   int det;        // J/K outputs are fixed-point integer accumulators (deterministic order)
   int* status;    // bounds-checked builds: first failed check (code, then the index), else unused
+  const double* rys;  // Rys roots and weights table (rys.cuh layout)
 };
 
 // Bounds-checked build (-DHF_BOUNDS_CHECK, small cases in place of a memory
@@ -128,10 +129,19 @@ struct JKWork {
   int nitems;
   int* counter;     // work-item counter, zero before the launch
   int chunk;        // kets per work item (32, or 1 for warp-cooperative classes)
+  int nchunk;       // Rys lists: each item's nsplit parts are nchunk output chunks times
+                    // ranges of primitive quartets (part = range * nchunk + chunk); 0 otherwise
 };
 
-// pair class of (la, lb), la >= lb: ss 0, ps 1, pp 2, ds 3, dp 4, dd 5
+// pair class of (la, lb), la >= lb: ss 0, ps 1, pp 2, ds 3, dp 4, dd 5, fs 6, ... gg 14
 __host__ __device__ inline int pair_class(int la, int lb) { return la * (la + 1) / 2 + lb; }
+// inverse of pair_class: (la, lb) of pair class X
+__host__ __device__ inline void pair_ls(int X, int* la, int* lb) {
+  int l = 0;
+  while ((l + 1) * (l + 2) / 2 <= X) ++l;
+  *la = l;
+  *lb = X - l * (l + 1) / 2;
+}
 __host__ __device__ inline int class_index(int la, int lb, int lc, int ld) {
   const int x = pair_class(la, lb), y = pair_class(lc, ld);
   return x * (x + 1) / 2 + y;
@@ -149,19 +159,23 @@ struct EriClassOps {
   jk_launch_fn jk64;
   jk_launch_fn jk32;
   jk_launch_fn jkdf;  // df64 variant
+  jk_launch_fn jkrys; // Rys-quadrature route (HF_JK_RYS; the only route of the f/g classes)
   store_launch_fn store;
   schwarz_launch_fn schwarz;
   occ_fn occ64;
   occ_fn occ32;
   occ_fn occdf;
+  occ_fn occrys;
   int chunk;      // kets per work item: 32 (warp of quartets) or 1 (warp-cooperative class)
+  int rys_nchunks;  // output chunks per quartet of the Rys kernel (every class)
+  int rys_native;   // the class has an f or g shell: only the Rys kernel serves it
   int vrr_flops;  // per primitive quartet, as generated
   int hrr_flops;  // per contracted quartet
   const char* name;
 };
 
 #ifndef HF_NCLASS
-#define HF_NCLASS 21
+#define HF_NCLASS 120
 #endif
 
 // Filled by the per-class translation units.
@@ -172,3 +186,5 @@ void hf_register_classes_d3(EriClassOps* table);
 void hf_register_classes_d4(EriClassOps* table);
 void hf_register_classes_d5(EriClassOps* table);
 void hf_register_classes_d6(EriClassOps* table);
+// Rys route: every class's jkrys, and all kernels of the f/g classes
+void hf_register_classes_rys(EriClassOps* table);

@@ -41,6 +41,7 @@ struct hf_ctx {
   double* boys64 = nullptr;
   float* boys32 = nullptr;
   float* boysdf = nullptr;
+  double* rys = nullptr;    // Rys roots and weights table (rys.cuh)
   EriClassOps ops[HF_NCLASS] = {};
   static constexpr int kSide = 4;
   cudaStream_t side[kSide] = {};     // class launches fork onto these (multi-molecule J/K)
@@ -150,6 +151,7 @@ struct hf_basis {
   // work lists for (tau, fp32_bound)
   bool have_work = false;
   double work_tau = -1.0, work_fp32 = -1.0;
+  bool work_rys = false;
   ClassWork work64[HF_NCLASS], work32[HF_NCLASS];
   DevArray<int> counters;             // 2 * HF_NCLASS
 
@@ -166,7 +168,10 @@ struct hf_basis {
   bool have_one = false;
 };
 
-int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound);
+// Work lists for (tau, fp32_bound); HF_JK_RYS in flags builds every class's
+// lists for the Rys kernel (one ket per item, items split into output
+// chunks and primitive ranges), as the f/g classes always are.
+int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound, unsigned flags);
 
 inline PairSet hf_pairset(const hf_basis* b) {
   return PairSet{b->prim64.ptr, b->prim32.ptr, b->pinfo.ptr, b->primdf.ptr, b->npairs, b->nprimpairs};
@@ -177,7 +182,7 @@ inline PairSet hf_pairset(const hf_basis* b) {
 inline KernelCommon hf_kernel_common(const hf_ctx* c, unsigned jk_flags) {
   const int f32 = (jk_flags & HF_JK_FP32_BOYS) ? 1 : 0;
   const int df = (!f32 && (jk_flags & HF_JK_DF64)) ? 1 : 0;
-  return KernelCommon{c->boys64, c->boys32, f32, c->boysdf, df, 0, c->bounds};  // det: set by hf_jk_run only
+  return KernelCommon{c->boys64, c->boys32, f32, c->boysdf, df, 0, c->bounds, c->rys};  // det: set by hf_jk_run only
 }
 // HF_JK_DETERMINISTIC is served by hf_fock_jk, hf_fock_jk_profiled and
 // hf_fock_jk_uhf; the entry points that build J/K elsewhere reject it.
@@ -186,12 +191,20 @@ inline int hf_reject_deterministic(unsigned jk_flags, const char* who) {
              ? hf_fail(HF_ERR_INVALID, "%s: HF_JK_DETERMINISTIC is served by hf_fock_jk and hf_fock_jk_uhf only", who)
              : HF_OK;
 }
-// launcher for the higher-precision work of a class: df64 when requested
+// launcher for the higher-precision work of a class: df64 when requested,
+// the Rys route for every class under HF_JK_RYS
 inline jk_launch_fn hf_jk_hi(const EriClassOps& op, unsigned jk_flags) {
-  return (jk_flags & HF_JK_DF64) ? op.jkdf : op.jk64;
+  return (jk_flags & HF_JK_RYS) ? op.jkrys : (jk_flags & HF_JK_DF64) ? op.jkdf : op.jk64;
 }
 inline int hf_occ_hi(const EriClassOps& op, unsigned jk_flags) {
-  return (jk_flags & HF_JK_DF64) ? op.occdf() : op.occ64();
+  return (jk_flags & HF_JK_RYS) ? op.occrys() : (jk_flags & HF_JK_DF64) ? op.occdf() : op.occ64();
+}
+// launcher for the reduced-precision (below fp32_bound) work of a class
+inline jk_launch_fn hf_jk_lo(const EriClassOps& op, unsigned jk_flags) {
+  return (jk_flags & HF_JK_RYS) ? op.jkrys : op.jk32;
+}
+inline int hf_occ_lo(const EriClassOps& op, unsigned jk_flags) {
+  return (jk_flags & HF_JK_RYS) ? op.occrys() : op.occ32();
 }
 int hf_basis_one_electron(hf_basis* b);  // fills b->S, T, V
 int hf_fock_jk_device(hf_basis* b, const double* D, double* J, double* K, const hf_jk_opts& o,

@@ -80,8 +80,8 @@ int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vec
         const int cnt = cw.kend_h[e] - cw.kbeg_h[e];
         const int nsp = cw.nsplit_h.empty() ? 1 : cw.nsplit_h[e];
         // item offsets are int on the device: checked in 64 bits per entry
-        const long long next =
-            (long long)hio.back() + (long long)((cnt + ctx->ops[cls].chunk - 1) / ctx->ops[cls].chunk) * nsp;
+        const int chunk = cw.w.chunk > 0 ? cw.w.chunk : 1;
+        const long long next = (long long)hio.back() + (long long)((cnt + chunk - 1) / chunk) * nsp;
         if (next > (1 << 30)) return hf_fail(HF_ERR_TOO_LARGE, "batched class %d: too many work items", cls);
         hb.push_back(cw.bra_h[e]);
         hkb.push_back(cw.kbeg_h[e]);
@@ -119,7 +119,9 @@ int MultiJK::build(hf_ctx* c, const std::vector<hf_basis*>& mols, const std::vec
     wk.nbra = nb;
     wk.nitems = hio.back();
     wk.counter = counters.ptr + c2;
-    wk.chunk = ctx->ops[cls].chunk;
+    // every molecule's lists were prepared with the same options
+    wk.chunk = nmol > 0 ? (r == 0 ? mols[0]->work64[cls] : mols[0]->work32[cls]).w.chunk : ctx->ops[cls].chunk;
+    wk.nchunk = nmol > 0 ? (r == 0 ? mols[0]->work64[cls] : mols[0]->work32[cls]).w.nchunk : 0;
     nquartets[c2] = nq;
     // the host vectors are reused for the next class: let the copies finish
     HF_CUDA(cudaStreamSynchronize(st));
@@ -177,11 +179,11 @@ int MultiJK::launch(const KernelCommon& kc, double* class_ms) {
       const JKWork& wk = w[2 * cls + r];
       if (wk.nitems <= 0) continue;
       any = true;
-      const int occ = std::max(r == 0 ? hf_occ_hi(op, jk_flags) : op.occ32(), 1);
+      const int occ = std::max(r == 0 ? hf_occ_hi(op, jk_flags) : hf_occ_lo(op, jk_flags), 1);
       const LaunchShape sh = hf_launch_shape(ctx, occ, wk.nitems, grid_scale[cls]);
       cudaStream_t ls = fork ? ctx->side[nlaunch++ % hf_ctx::kSide] : st;
       NvtxRange nv_cls(op.name);
-      (r == 0 ? hf_jk_hi(op, jk_flags) : op.jk32)(wk, none, kc, one, table.ptr, sh.grid, sh.threads, ls);
+      (r == 0 ? hf_jk_hi(op, jk_flags) : hf_jk_lo(op, jk_flags))(wk, none, kc, one, table.ptr, sh.grid, sh.threads, ls);
     }
     if (class_ms && any) {
       HF_CUDA(cudaEventRecord(ev[1], st));
@@ -253,6 +255,7 @@ int MultiJK::capture(const KernelCommon& kc) {
     ctx->ops[c].occ64();
     ctx->ops[c].occ32();
     ctx->ops[c].occdf();
+    ctx->ops[c].occrys();
   }
   HF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   capturing = true;

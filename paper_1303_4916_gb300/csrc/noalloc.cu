@@ -28,9 +28,10 @@
 
 #define HF_NOALLOC_MAX_NBF 512
 #define HF_NOALLOC_NN ((size_t)HF_NOALLOC_MAX_NBF * HF_NOALLOC_MAX_NBF)
-#define HF_NOALLOC_COUNTER_DOUBLES 64  // room for 2 * HF_NCLASS int counters
+#define HF_NOALLOC_COUNTER_DOUBLES 128  // room for 2 * HF_NCLASS int counters
 
 // [0, NN): J' ; [NN, 2NN): K' ; then the work-item counters (as int).
+static_assert(HF_NOALLOC_COUNTER_DOUBLES * 2 >= 2 * HF_NCLASS, "counter room");
 static __device__ __align__(256) double g_noalloc_scratch[2 * HF_NOALLOC_NN + HF_NOALLOC_COUNTER_DOUBLES];
 
 namespace {
@@ -73,7 +74,8 @@ extern "C" int hf_fock_jk_noalloc(hf_basis* b, const double* D, double* J, doubl
                    HF_NOALLOC_MAX_NBF);
   hf_ctx* ctx = b->ctx;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  if (!b->have_work || b->work_tau != o.schwarz_tau || b->work_fp32 != o.fp32_bound)
+  if (!b->have_work || b->work_tau != o.schwarz_tau || b->work_fp32 != o.fp32_bound ||
+      b->work_rys != ((o.flags & HF_JK_RYS) != 0))
     return hf_fail(HF_ERR_INVALID,
                    "hf_fock_jk_noalloc: no quartet work lists for these options on this basis; call hf_fock_jk or "
                    "hf_count_quartets once with the same options first (that call allocates)");

@@ -13,10 +13,17 @@
 //                       Th(0)^(m) = 2 pi / p exp(-ab/p |AB|^2) F_m(p |PC|^2)
 //                       (a|b) from Th(a+k) by the binomial transfer
 //                       (x-B)^b = sum_k C(b,k) (x-A)^k (A-B)^(b-k).
+//   for la + lb > 4 (f and g shells) the nuclear attraction is taken by Rys
+//   quadrature instead: with n = (la+lb)/2 + 1 roots u of the rule at
+//   T = p |PC|^2, (a|1/r_C|b) = 2 pi / p exp(-ab/p |AB|^2)
+//   sum_u w_u Ix Iy Iz, the one-dimensional factors from
+//                       I(i+1) = (PA - u PC) I(i) + i (1 - u) / (2p) I(i-1),
+//                       I(0) = 1, and the same transfer to B.
 #include <cmath>
 
 #include "eri.cuh"
 #include "hf_internal.h"
+#include "rys.cuh"
 
 namespace {
 
@@ -27,6 +34,19 @@ __device__ __forceinline__ void cart_pow(int l, int c, int* p) {
       if (k == c) { p[0] = x; p[1] = y; p[2] = l - x - y; return; }
       ++k;
     }
+}
+
+// scale of Cartesian component c of an axial-normalised shell of angular
+// momentum l: sqrt((2l-1)!! / ((2x-1)!! (2y-1)!! (2z-1)!!))
+__device__ double comp_scale_any(int l, int c) {
+  int p[3];
+  cart_pow(l, c, p);
+  auto df = [](int x) {
+    double r = 1.0;
+    for (int k = 2 * x - 1; k > 1; k -= 2) r *= k;
+    return r;
+  };
+  return sqrt(df(l) / (df(p[0]) * df(p[1]) * df(p[2])));
 }
 
 __device__ double binom(int n, int k) {
@@ -51,8 +71,8 @@ __global__ void one_electron_kernel(int nbf, const int* __restrict__ bf_shell, c
                                     const int* __restrict__ sh_prim, const double* __restrict__ sh_xyz,
                                     const double* __restrict__ exps, const double* __restrict__ coefs, int natom,
                                     const double* __restrict__ atom_xyz, const int* __restrict__ atom_Z,
-                                    const double* __restrict__ boys, double* __restrict__ S, double* __restrict__ T,
-                                    double* __restrict__ V) {
+                                    const double* __restrict__ boys, const double* __restrict__ rys,
+                                    double* __restrict__ S, double* __restrict__ T, double* __restrict__ V) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)nbf * nbf) return;
   const int i = (int)(t / nbf), j = (int)(t % nbf);
@@ -63,7 +83,7 @@ __global__ void one_electron_kernel(int nbf, const int* __restrict__ bf_shell, c
   cart_pow(lb, j - sh_bf[sb], pb);
   const double* A = sh_xyz + 3 * sa;
   const double* B = sh_xyz + 3 * sb;
-  const double scale = hfk::comp_scale(la, i - sh_bf[sa]) * hfk::comp_scale(lb, j - sh_bf[sb]);
+  const double scale = comp_scale_any(la, i - sh_bf[sa]) * comp_scale_any(lb, j - sh_bf[sb]);
   double AB[3], r2 = 0.0;
   for (int x = 0; x < 3; ++x) {
     AB[x] = A[x] - B[x];
@@ -81,14 +101,14 @@ __global__ void one_electron_kernel(int nbf, const int* __restrict__ bf_shell, c
         PA[x] = P[x] - A[x];
         PB[x] = P[x] - B[x];
       }
-      // 1D overlaps S[x][i][j], i <= 2, j <= 4
-      double S1[3][3][5];
+      // 1D overlaps S[x][i][j], i <= la, j <= lb + 2
+      double S1[3][5][7];
       for (int x = 0; x < 3; ++x) {
-        double (*s)[5] = S1[x];
+        double (*s)[7] = S1[x];
         s[0][0] = sqrt(3.14159265358979323846 / p) * exp(-mu * AB[x] * AB[x]);
-        for (int ii = 0; ii < 2; ++ii) s[ii + 1][0] = PA[x] * s[ii][0] + (ii > 0 ? ii * o2p * s[ii - 1][0] : 0.0);
-        for (int ii = 0; ii <= 2; ++ii)
-          for (int jj = 0; jj < 4; ++jj)
+        for (int ii = 0; ii < pa[x]; ++ii) s[ii + 1][0] = PA[x] * s[ii][0] + (ii > 0 ? ii * o2p * s[ii - 1][0] : 0.0);
+        for (int ii = 0; ii <= pa[x]; ++ii)
+          for (int jj = 0; jj < pb[x] + 2; ++jj)
             s[ii][jj + 1] = PB[x] * s[ii][jj] + ((ii > 0 ? ii * s[ii - 1][jj] : 0.0) + (jj > 0 ? jj * s[ii][jj - 1] : 0.0)) * o2p;
       }
       const double sx = S1[0][pa[0]][pb[0]], sy = S1[1][pa[1]][pb[1]], sz = S1[2][pa[2]][pb[2]];
@@ -108,6 +128,28 @@ __global__ void one_electron_kernel(int nbf, const int* __restrict__ bf_shell, c
         if (atom_Z[at] == 0) continue;
         const double* Cc = atom_xyz + 3 * at;
         double PC[3] = {P[0] - Cc[0], P[1] - Cc[1], P[2] - Cc[2]};
+        if (L > 4) {  // Rys quadrature
+          const int nr = L / 2 + 1;
+          const double Tn = p * (PC[0] * PC[0] + PC[1] * PC[1] + PC[2] * PC[2]);
+          double vr = 0.0;
+          for (int r = 0; r < nr; ++r) {
+            double u, w;
+            rys_rule_root(rys, nr, r, Tn, &u, &w);
+            double prod = w;
+            for (int x = 0; x < 3; ++x) {
+              double g[9];
+              g[0] = 1.0;
+              const double c00 = PA[x] - u * PC[x], b10 = (1.0 - u) * o2p;
+              for (int k = 0; k < pa[x] + pb[x]; ++k) g[k + 1] = c00 * g[k] + (k > 0 ? k * b10 * g[k - 1] : 0.0);
+              double v = 0.0;
+              for (int k = 0; k <= pb[x]; ++k) v += binom(pb[x], k) * pow(AB[x], pb[x] - k) * g[pa[x] + k];
+              prod *= v;
+            }
+            vr += prod;
+          }
+          v_sum -= c * atom_Z[at] * pre * vr;
+          continue;
+        }
         double F[5];
         boys_any(L, p * (PC[0] * PC[0] + PC[1] * PC[1] + PC[2] * PC[2]), boys, F);
         // Th[ex][ey][ez][m], total l <= 4
@@ -195,7 +237,7 @@ int hf_basis_one_electron(hf_basis* b) {
   const long long tot = (long long)n * n;
   one_electron_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(
       n, dbs.ptr, dl.ptr, dbf.ptr, dn.ptr, dp.ptr, dsx.ptr, dex.ptr, dco.ptr, b->natom, dax.ptr, dZ.ptr, ctx->boys64,
-      b->S.ptr, b->T.ptr, b->V.ptr);
+      ctx->rys, b->S.ptr, b->T.ptr, b->V.ptr);
   HF_CUDA(cudaGetLastError());
   HF_CUDA(cudaStreamSynchronize(st));
   b->have_one = true;

@@ -484,7 +484,7 @@ extern "C" int hf_scf_solve(hf_basis* b, const hf_scf_opts* opts, hf_scf_result*
   MultiJK mj;
   const KernelCommon kc = hf_kernel_common(ctx, o.jk.flags);
   if (!G.ptr) {
-    HF_CHECK(hf_basis_prepare_work(b, o.jk.schwarz_tau, o.jk.fp32_bound));
+    HF_CHECK(hf_basis_prepare_work(b, o.jk.schwarz_tau, o.jk.fp32_bound, o.jk.flags));
     mj.jk_flags = o.jk.flags;
     HF_CHECK(mj.build(ctx, {b}, {s.D.ptr}, {s.J.ptr}, {s.K.ptr}));
     HF_CHECK(mj.capture(kc));
@@ -657,7 +657,7 @@ extern "C" int hf_uhf_solve(hf_basis* b, int n_alpha, int n_beta, const hf_scf_o
   HF_CHECK(scf_setup(b, s));
   HF_CUDA(cudaMemcpyAsync(u.F2.ptr, s.H.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
   HF_CUDA(cudaMemcpyAsync(u.F2.ptr + nn, s.H.ptr, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  HF_CHECK(hf_basis_prepare_work(b, o.jk.schwarz_tau, o.jk.fp32_bound));
+  HF_CHECK(hf_basis_prepare_work(b, o.jk.schwarz_tau, o.jk.fp32_bound, o.jk.flags));
   MultiJK mj;
   mj.jk_flags = o.jk.flags;
   const KernelCommon kc = hf_kernel_common(ctx, o.jk.flags);

@@ -133,7 +133,7 @@ void hf_server::run() {
       int rc = hf_basis_create(ctx, r->atoms.data(), (int)r->atoms.size(), r->shells.data(), (int)r->shells.size(),
                                r->exps.data(), r->coefs.data(), r->nelec, &r->basis);
       r->scf.reset(new ScfState());
-      if (rc == HF_OK) rc = hf_basis_prepare_work(r->basis, opts.scf.jk.schwarz_tau, opts.scf.jk.fp32_bound);
+      if (rc == HF_OK) rc = hf_basis_prepare_work(r->basis, opts.scf.jk.schwarz_tau, opts.scf.jk.fp32_bound, opts.scf.jk.flags);
       if (rc == HF_OK) rc = scf_state_init(r->basis, *r->scf, opts.scf.diis_size);
       if (rc == HF_OK) rc = scf_begin(r->basis, *r->scf, opts.scf, nullptr);
       std::lock_guard<std::mutex> lk(mu);

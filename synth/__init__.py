@@ -7,6 +7,7 @@ integrals and SCF live on the two sides that consume these inputs (the CPU
 oracle under ``oracle/`` and the CUDA library), each with its own code.
 """
 from .molecules import (  # noqa: F401
+    water_qz,
     Molecule,
     h_line,
     lattice_molecule,

@@ -8,7 +8,7 @@ range built from the rules below.  Every draw comes from
 charges, then for each shell its exponents followed by its coefficients.
 
 Coordinates are in bohr, as in the paper's input file (Sec. "Using the
-code").  Shell angular momentum l is 0, 1 or 2 (Cartesian s, p, d).
+code").  Shell angular momentum l is 0..4 (Cartesian s, p, d, f, g).
 Coefficients are raw draws; normalisation (Eq. 1 basis functions with unit
 self-overlap) is left to the consumer.
 """
@@ -133,6 +133,7 @@ BASIS_RULES = {
     "sp": dict(h=[0, 0], heavy=[0, 0, 0, 1, 1], nprim=(3, 3), exp=(0.05, 50.0)),
     "spd": dict(h=[0, 0], heavy=[0, 0, 0, 1, 1, 2], nprim=(1, 6), exp=(0.03, 200.0)),
     "s": dict(h=[0], heavy=[0, 0], nprim=(3, 3), exp=(0.1, 10.0)),
+    "spdfg": dict(h=[0, 0, 1], heavy=[0, 0, 0, 1, 1, 2, 3, 4], nprim=(1, 3), exp=(0.1, 30.0)),
 }
 
 
@@ -167,6 +168,49 @@ def lattice_molecule(n_atoms: int, seed: int, rules: str = "sp",
     m = _pack(Z, xyz, shells, f"lattice{n_atoms}_{rules}_s{seed}", seed)
     m.meta["rules"] = rules
     return m
+
+
+# Shape of a correlation-consistent quadruple-zeta basis, the basis of the
+# paper's HF timing benchmark (H2O, Fig. 4): per element, the shells as
+# (l, primitives).  O: 5s4p3d2f1g with two s shells contracted over 12
+# primitives and one p shell over 6; H: 4s3p2d1f with one s shell over 4.
+QZ_SHAPE = {
+    8: [(0, 12), (0, 12), (0, 1), (0, 1), (0, 1), (1, 6), (1, 1), (1, 1), (1, 1),
+        (2, 1), (2, 1), (2, 1), (3, 1), (3, 1), (4, 1)],
+    1: [(0, 4), (0, 1), (0, 1), (0, 1), (1, 1), (1, 1), (1, 1), (2, 1), (2, 1), (3, 1)],
+}
+# exponent range per element and l (contracted shells draw log-uniform in
+# it; the single-primitive shells of one l are even-tempered across it with
+# a jitter of 0.2 of a step)
+QZ_EXP = {
+    8: {0: (0.1, 6.0e4), 1: (0.1, 60.0), 2: (0.3, 4.0), 3: (0.5, 3.0), 4: (1.0, 2.5)},
+    1: {0: (0.05, 80.0), 1: (0.2, 3.0), 2: (0.5, 2.5), 3: (0.8, 1.5)},
+}
+
+
+def water_qz(seed: int = 0, coef_range=(0.2, 1.0)) -> Molecule:
+    """H2O (O-H 1.809 bohr, H-O-H 104.5 degrees) with a synthetic basis of
+    the quadruple-zeta shape above: nbf 140 (Cartesian), 10 electrons."""
+    rng = np.random.default_rng(seed)
+    half = np.deg2rad(104.5) / 2
+    r = 1.809
+    xyz = np.array([[0.0, 0.0, 0.0], [r * np.sin(half), r * np.cos(half), 0.0],
+                    [-r * np.sin(half), r * np.cos(half), 0.0]])
+    Z = [8, 1, 1]
+    shells = []
+    for a, z in enumerate(Z):
+        spec = QZ_SHAPE[z]
+        for l in sorted({l for l, _ in spec}):
+            lo, hi = QZ_EXP[z][l]
+            single = [k for ll, k in spec if ll == l and k == 1]
+            for ll, k in spec:
+                if ll == l and k > 1:
+                    shells.append((a, l, _log_uniform(rng, lo, hi, k), rng.uniform(*coef_range, size=k)))
+            ns = len(single)
+            for i in range(ns):
+                t = (i + 0.5 + rng.uniform(-0.2, 0.2)) / ns
+                shells.append((a, l, np.array([lo * (hi / lo) ** t]), np.array([1.0])))
+    return _pack(Z, xyz, shells, f"water_qz_s{seed}", seed)
 
 
 def random_shells_molecule(ls, seed: int, nprim=(1, 3), exp_range=(0.2, 3.0),

@@ -268,7 +268,7 @@ def test_errors(ctx, hf):
     assert e.value.code == -8
     bad = mol.copy()
     bad.shell_l = bad.shell_l.copy()
-    bad.shell_l[0] = 3
+    bad.shell_l[0] = 5   # above HF_LMAX (g)
     with pytest.raises(hf.HFError) as e:
         hf.Basis(ctx, bad)
     assert e.value.code == -2
@@ -411,3 +411,41 @@ def test_scf_restart_from_density(ctx, hf):
     r2 = b.scf(max_iter=128, e_tol=1e-10, diis_size=8, D0=r.tensors["D"])
     assert r2.converged and r2.iterations <= 3
     assert abs(r2.energy - r.energy) <= 1e-9
+
+
+def _max_prim_atom(nprim, seed):
+    """One atom carrying an s and a p shell of nprim primitives and a d shell
+    of three (exponents log-uniform in [0.05, 50], coefficients U[0.2, 1])."""
+    from synth.molecules import _pack
+    rng = np.random.default_rng(seed)
+    shells = []
+    for l, k in ((0, nprim), (1, nprim), (2, 3)):
+        e = np.exp(rng.uniform(np.log(0.05), np.log(50.0), k))
+        shells.append((0, l, list(e), list(rng.uniform(0.2, 1.0, k))))
+    return _pack([8], [[0.1, -0.2, 0.3]], shells, "maxprim", seed, n_electrons=8)
+
+
+def test_single_centre_and_maximum_primitives(ctx, hf):
+    """Edge cases of the integral path against the oracle: all four centres of
+    every quartet coincide (one atom with s, p and d shells: A - B = C - D =
+    P - Q = 0, Boys argument T = 0) and the s and p shells have the maximum of
+    HF_MAX_NPRIM primitives (16^4 primitive quartets in (pp|pp), the longest
+    primitive loops the kernels and their split items see), for the ERI
+    tensor, J/K in the FP64 and df64 tiers and the Schwarz factors; one
+    primitive more is refused."""
+    from paper_1303_4916_gb300 import _abi
+    mol = _max_prim_atom(_abi.HF_MAX_NPRIM, 5)
+    ob = oracle.Basis(mol)
+    b = hf.Basis(ctx, mol)
+    G = b.eri_tensor().cpu().numpy()
+    assert np.abs(G - ob.eri_tensor()).max() <= ERI_TOL
+    assert np.allclose(b.schwarz(), ob.schwarz(), rtol=1e-11, atol=1e-14)
+    D = _density(ob.nbf, 9)
+    J0, K0, _ = ob.jk(D, tau=0.0, nthreads=oracle.oracle_threads())
+    for tier in ({}, {"df64": True}):
+        J, K = b.fock_jk(_t(D), opts=hf.jk_opts(schwarz_tau=0.0, **tier))
+        assert np.abs(J.cpu().numpy() - J0).max() <= JK_TOL, tier
+        assert np.abs(K.cpu().numpy() - K0).max() <= JK_TOL, tier
+    with pytest.raises(hf.HFError) as e:
+        hf.Basis(ctx, _max_prim_atom(_abi.HF_MAX_NPRIM + 1, 5))
+    assert e.value.code == _abi.HF_ERR_INVALID
