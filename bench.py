@@ -482,7 +482,7 @@ def run_ours(args):
     achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
     sm_count = ctx.num_sms
     peak = fp64_alu_peak(sm_count, 2070.0)
-    cls_name = f"({'spd'[s.la]}{'spd'[s.lb]}|{'spd'[s.lc]}{'spd'[s.ld]})"
+    cls_name = f"({'spdfg'[s.la]}{'spdfg'[s.lb]}|{'spdfg'[s.lc]}{'spdfg'[s.ld]})"
     traffic = ncu_traffic(cls_name)
     all_ms = float(prof[:, 0].sum() + prof[:, 1].sum())
     all_flops = sum(flops)
@@ -495,7 +495,7 @@ def run_ours(args):
     d_ms = float(prof_df[ddom, 0])
     d_ach = ops_pq * sd.prim_quartets_fp64 / (d_ms * 1e-3) / 1e12
     d_peak = fp32_alu_peak(sm_count, 2070.0)
-    d_name = f"({'spd'[sd.la]}{'spd'[sd.lb]}|{'spd'[sd.lc]}{'spd'[sd.ld]})"
+    d_name = f"({'spdfg'[sd.la]}{'spdfg'[sd.lb]}|{'spdfg'[sd.lc]}{'spdfg'[sd.ld]})"
     roofline_df64 = {"bound": "alu", "achieved": d_ach, "peak": d_peak, "unit": "T FP32-op/s",
                      "frac": d_ach / d_peak, "traffic": ncu_traffic(d_name, "df64"),
                      "kernel": f"eri_jk_kernel {d_name} df64", "kernel_ms": d_ms,
@@ -535,6 +535,10 @@ def run_ours(args):
                                               args.oracle_budget, oracle_background=pending)
         except Exception as e:
             extras["serving"] = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            extras["rys_water_qz"] = rys_water_qz()
+        except Exception as e:
+            extras["rys_water_qz"] = {"error": f"{type(e).__name__}: {e}"}
         try:
             left = args.extras_budget - (time.perf_counter() - t_ex)
             extras["c3_150_atom"] = measure_c3(budget_s=max(0.0, left), modes=("fp32_split_df64", "fp64"))
@@ -959,6 +963,149 @@ def run_serve(args):
                       "config": {"workload": r["workload"]}, **r}), flush=True)
 
 
+def rys_water_qz(steps=10, warmup=3, cluster=8):
+    """H2O in the synthetic quadruple-zeta-shaped basis (synth.water_qz(0):
+    O 5s4p3d2f1g, H 4s3p2d1f; nbf 140), the shape of the paper's HF timing
+    benchmark: every quartet with an f or g shell runs on the Rys-quadrature
+    kernel.  Returns the RHF solve (time, iterations, |dE| against the
+    stored oracle energy), FP64 J/K builds/s at the converged density
+    (Schwarz tau 1e-12, L2 flushed between timed builds, CUDA events on the
+    library stream) and the Rys kernels' FP64 roofline: counted operations
+    per primitive quartet (recurrences, transfers, products; an FMA counts
+    2) over the class kernels timed one by one."""
+    import torch
+    import paper_1303_4916_gb300 as hf
+    from synth import water_qz
+    ref = json.load(open(os.path.join(ROOT, "tests", "golden", "water_qz.json")))
+    ctx = hf.Context(0)
+    mol = water_qz(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    basis = hf.Basis(ctx, mol)
+    r = basis.scf(max_iter=100, e_tol=1e-10, diis_size=8, schwarz_tau=0.0)
+    torch.cuda.synchronize()
+    scf_s = time.perf_counter() - t0
+    D = r.tensors["D"]
+    o = hf.jk_opts()
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=D.device)
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        basis.fock_jk(D, J, K, o)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        basis.fock_jk(D, J, K, o)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    prof = basis.fock_jk_profiled(D, J, K, o)
+    stats = basis.class_stats(o)
+    rys_ms = rys_flops = 0.0
+    dom = (0.0, None, 0.0)
+    for c, sc in enumerate(stats):
+        if max(sc.la, sc.lb, sc.lc, sc.ld) < 3:
+            continue
+        t = float(prof[c, 0] + prof[c, 1])
+        f = (sc.prim_quartets_fp64 + sc.prim_quartets_fp32) * sc.prim_flops + \
+            (sc.quartets_fp64 + sc.quartets_fp32) * (sc.hrr_flops + sc.digest_flops)
+        rys_ms += t
+        rys_flops += f
+        if t > dom[0]:
+            dom = (t, sc, f)
+    peak = fp64_alu_peak(ctx.num_sms, 2070.0)
+    ach = rys_flops / (rys_ms * 1e-3) / 1e12 if rys_ms > 0 else 0.0
+    out = {"workload": "H2O, synthetic quadruple-zeta-shaped basis (synth.water_qz(0); O 5s4p3d2f1g, H 4s3p2d1f, "
+                       "contracted s/p, single-primitive polarisation shells), nbf 140",
+           "nbf": int(basis.nbf), "scf_s": scf_s, "scf_iterations": int(r.iterations),
+           "energy": r.energy, "abs_dE_vs_oracle": abs(r.energy - ref["energy"]),
+           "jk_ms": statistics.median(ms), "builds_per_s": 1000.0 / statistics.median(ms),
+           "class_ms_serial_total": float(prof.sum()), "rys_class_ms_serial": rys_ms,
+           "rys_share_serial": rys_ms / float(prof.sum()) if prof.sum() > 0 else 0.0,
+           "roofline_rys": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                            "scope": "all f/g class kernels, each timed alone",
+                            "peak_note": "FP64 nominal: 152 SM x 2 DFMA x 2 x 2.07 GHz"}}
+    if dom[1] is not None:
+        sc = dom[1]
+        name = f"({'spdfg'[sc.la]}{'spdfg'[sc.lb]}|{'spdfg'[sc.lc]}{'spdfg'[sc.ld]})"
+        out["rys_dominant"] = {"class": name, "ms": dom[0], "prim_quartets": int(sc.prim_quartets_fp64),
+                               "flops_per_prim_quartet": int(sc.prim_flops),
+                               "tflops": dom[2] / (dom[0] * 1e-3) / 1e12}
+    basis.close()
+    if cluster > 0:
+        out["cluster"] = rys_cluster(ctx, cluster, steps=max(2, steps // 3))
+    return out
+
+
+def rys_class_roofline(basis, D, o, peak):
+    """FP64 roofline of the f/g (Rys) class kernels of one J/K build: counted
+    operations over the class kernels timed one by one."""
+    import torch
+    prof = basis.fock_jk_profiled(D, torch.empty_like(D), torch.empty_like(D), o)
+    stats = basis.class_stats(o)
+    ms = fl = 0.0
+    for c, sc in enumerate(stats):
+        if max(sc.la, sc.lb, sc.lc, sc.ld) < 3:
+            continue
+        ms += float(prof[c, 0] + prof[c, 1])
+        fl += (sc.prim_quartets_fp64 + sc.prim_quartets_fp32) * sc.prim_flops + \
+            (sc.quartets_fp64 + sc.quartets_fp32) * (sc.hrr_flops + sc.digest_flops)
+    ach = fl / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "rys_class_ms_serial": ms, "class_ms_serial_total": float(prof.sum()),
+            "scope": "all f/g class kernels, each timed alone"}
+
+
+def rys_cluster(ctx, n, steps=3):
+    """n QZ-shaped waters (synth.water_cluster_qz; nbf 140 n): FP64 J/K
+    builds/s for a seeded density C C^T (C: nbf x 5n Gaussian / sqrt(nbf);
+    the work, set by Schwarz screening, does not depend on D) and the Rys
+    kernels' roofline."""
+    import torch
+    import paper_1303_4916_gb300 as hf
+    from synth import water_cluster_qz
+    mol = water_cluster_qz(n, 0)
+    basis = hf.Basis(ctx, mol)
+    nb = basis.nbf
+    rng = np.random.default_rng(5)
+    Cm = rng.normal(size=(nb, 5 * n)) / np.sqrt(nb)
+    D = torch.tensor(Cm @ Cm.T, dtype=torch.float64, device="cuda:0")
+    o = hf.jk_opts()
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    basis.fock_jk(D, J, K, o)
+    st = torch.cuda.current_stream()
+    ms = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        basis.fock_jk(D, J, K, o)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    nq, _ = basis.count_quartets(o)
+    out = {"workload": f"{n} QZ-shaped waters on a 5.7-bohr cubic lattice (synth.water_cluster_qz({n}, 0)), "
+                       f"nbf {nb}, seeded density, Schwarz tau 1e-12",
+           "nbf": int(nb), "quartets": int(nq), "jk_ms": statistics.median(ms),
+           "builds_per_s": 1000.0 / statistics.median(ms),
+           "roofline_rys": rys_class_roofline(basis, D, o, fp64_alu_peak(ctx.num_sms, 2070.0))}
+    basis.close()
+    return out
+
+
+def run_rys(args):
+    """--workload rys: one JSON line for the quadruple-zeta-shaped water."""
+    r = rys_water_qz(args.steps, args.warmup, cluster=args.nwater)
+    print(json.dumps({"metric": "Fock(J+K) builds/s (H2O, QZ-shaped basis s..g)", "unit": "builds/s",
+                      "value": r["builds_per_s"], "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": r["workload"], "l2": "flushed between timed steps"}, **r}), flush=True)
+
+
 def run_setup(args):
     """Basis set-up (pair records, Schwarz factors, work lists) of the first
     --nreq molecules of the serving stream (atoms log-uniform [4, --atoms-max],
@@ -1027,7 +1174,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c1", "c3", "c3check", "batch", "serve", "classes", "setup"],
+                    choices=["c2", "c1", "c3", "c3check", "batch", "serve", "classes", "setup", "rys"],
                     help="c2 (default) is the benchmark line; the others print secondary measurements")
     ap.add_argument("--nmol", type=int, default=64)
     ap.add_argument("--nreq", type=int, default=24)
@@ -1042,6 +1189,7 @@ def main():
                     help="default run: skip the serving stream and the 150-atom builds")
     ap.add_argument("--c3-max-seconds", type=float, default=120.0)
     ap.add_argument("--natom", type=int, default=12)
+    ap.add_argument("--nwater", type=int, default=8, help="rys: waters in the throughput cluster (0 = none)")
     ap.add_argument("--fp32-bound", type=float, default=0.0)
     ap.add_argument("--e-tol", type=float, default=1e-8)
     ap.add_argument("--df64", action="store_true", help="serve, batch, classes: df64 tier above the FP32 bound")
@@ -1053,7 +1201,7 @@ def main():
         return run_reference(args)
     if args.workload != "c2":
         return {"c1": run_c1, "c3": run_c3, "c3check": run_c3check, "batch": run_batch, "serve": run_serve,
-                "classes": run_classes, "setup": run_setup}[args.workload](args)
+                "classes": run_classes, "setup": run_setup, "rys": run_rys}[args.workload](args)
     return run_ours(args)
 
 

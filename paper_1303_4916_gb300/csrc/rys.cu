@@ -325,6 +325,37 @@ inline RysClass rys_class_of(int cls) {
   return rys_class(la, lb, lc, ld);
 }
 
+__host__ __device__ inline int la1_(const RysClass& rc) { return rc.la + 1; }
+
+// Position (d0, d1, d2, d3) of a flat index in the mixed radix (3, n1, n2,
+// n3), d3 fastest, advanced by 32 per step with one carry per digit: the
+// transfer loops walk their entries without dividing.
+struct Radix {
+  int d[4];
+  int n[4];
+  int s[4];
+  __device__ Radix(int e, int n1, int n2, int n3) {
+    n[0] = 3; n[1] = n1; n[2] = n2; n[3] = n3;
+    d[3] = e % n3; e /= n3;
+    d[2] = e % n2; e /= n2;
+    d[1] = e % n1; d[0] = e / n1;
+    int t = 32;
+    s[3] = t % n3; t /= n3;
+    s[2] = t % n2; t /= n2;
+    s[1] = t % n1; s[0] = t / n1;
+  }
+  __device__ __forceinline__ void step() {
+    int c = 0;
+#pragma unroll
+    for (int k = 3; k >= 1; --k) {
+      d[k] += s[k] + c;
+      c = d[k] >= n[k];
+      if (c) d[k] -= n[k];
+    }
+    d[0] += s[0] + c;
+  }
+};
+
 __device__ __forceinline__ double dfact_odd(int x) {  // (2x-1)!!
   double r = 1.0;
   for (int k = 2 * x - 1; k > 1; k -= 2) r *= k;
@@ -405,6 +436,8 @@ __device__ void rys_rows(const RysClass& rc, const double* __restrict__ prim, co
 #pragma unroll
   for (int d = 0; d < 3; ++d) need[d] = __reduce_or_sync(0xffffffffu, need[d]);
   const int L1 = rc.nmax + 1, M1 = rc.mmax + 1;
+  // this lane's first entries of the two transfers, walked 32 at a time
+  const Radix hw(lane, la1_(rc), l1, M1), iw(lane, (rc.la + 1) * l1, rc.lc + 1, l3);
   const bool gl = lane < 3 * L1;
   const int gdir = gl ? lane / L1 : 0, gn = gl ? lane - gdir * L1 : 0;
   double* const ru = s + kRu;
@@ -455,12 +488,11 @@ __device__ void rys_rows(const RysClass& rc, const double* __restrict__ prim, co
       }
       __syncwarp();
       if (rc.lb > 0) {  // H(ia, ib, m) = sum_k C(ib,k) AB^(ib-k) G(ia + k, m)
-        for (int e = lane; e < 3 * rc.SH; e += 32) {
-          const int dir = e / rc.SH, r2 = e - dir * rc.SH;
-          const int m = r2 % M1, iab = r2 / M1;
+        Radix w = hw;
+        for (int e = lane; e < 3 * rc.SH; e += 32, w.step()) {
+          const int dir = w.d[0], ia = w.d[1], ib2 = w.d[2], m = w.d[3];
           const unsigned nd = dir == 0 ? need[0] : (dir == 1 ? need[1] : need[2]);
-          if (!((nd >> iab) & 1u)) continue;
-          const int ib2 = iab % l1, ia = iab / l1;
+          if (!((nd >> (ia * l1 + ib2)) & 1u)) continue;
           const double* g = s + rc.oG + dir * rc.SG + ia * M1 + m;
           const double* cf = s + kCb + (dir * 6 + ib2) * 6;
           double v = 0.0;
@@ -470,13 +502,11 @@ __device__ void rys_rows(const RysClass& rc, const double* __restrict__ prim, co
         __syncwarp();
       }
       if (rc.ld > 0) {  // I(iab, ic, id) = sum_k C(id,k) CD^(id-k) H(iab, ic + k)
-        for (int e = lane; e < 3 * rc.SI; e += 32) {
-          const int dir = e / rc.SI, r2 = e - dir * rc.SI;
-          const int iab = r2 / ncd_dir;
+        Radix w = iw;
+        for (int e = lane; e < 3 * rc.SI; e += 32, w.step()) {
+          const int dir = w.d[0], iab = w.d[1], ic = w.d[2], id = w.d[3];
           const unsigned nd = dir == 0 ? need[0] : (dir == 1 ? need[1] : need[2]);
           if (!((nd >> iab) & 1u)) continue;
-          const int icd = r2 - iab * ncd_dir;
-          const int id = icd % l3, ic = icd / l3;
           const double* h = s + rc.oH + dir * rc.SH + iab * M1 + ic;
           const double* cf = s + kCd + (dir * 6 + id) * 6;
           double v = 0.0;

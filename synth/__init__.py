@@ -8,6 +8,7 @@ oracle under ``oracle/`` and the CUDA library), each with its own code.
 """
 from .molecules import (  # noqa: F401
     water_qz,
+    water_cluster_qz,
     Molecule,
     h_line,
     lattice_molecule,

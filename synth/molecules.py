@@ -213,6 +213,35 @@ def water_qz(seed: int = 0, coef_range=(0.2, 1.0)) -> Molecule:
     return _pack(Z, xyz, shells, f"water_qz_s{seed}", seed)
 
 
+def water_cluster_qz(n: int = 8, seed: int = 0, spacing: float = 5.7) -> Molecule:
+    """n copies of water_qz(seed) (same basis on every copy, as a basis set
+    is per element) on a simple-cubic lattice of the given spacing (bohr),
+    each rotated by a random rotation (QR of a Gaussian 3x3 matrix, drawn
+    from default_rng(seed + 1) in molecule order): nbf 140 n, 10 n
+    electrons."""
+    w = water_qz(seed)
+    rng = np.random.default_rng(seed + 1)
+    m = 1
+    while m ** 3 < n:
+        m += 1
+    sites = [(i, j, k) for i in range(m) for j in range(m) for k in range(m)][:n]
+    Z, xyz, shells = [], [], []
+    com = w.xyz.mean(axis=0)
+    for c, site in enumerate(sites):
+        q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+        q = q * np.sign(np.diag(r))
+        if np.linalg.det(q) < 0:
+            q[:, 0] = -q[:, 0]
+        pos = (w.xyz - com) @ q.T + spacing * np.asarray(site, dtype=np.float64)
+        for a in range(w.natom):
+            Z.append(int(w.Z[a]))
+            xyz.append(pos[a])
+        for sh in range(w.nshell):
+            o, k = int(w.shell_prim[sh]), int(w.shell_nprim[sh])
+            shells.append((c * w.natom + int(w.shell_atom[sh]), int(w.shell_l[sh]), w.exps[o:o + k], w.coefs[o:o + k]))
+    return _pack(Z, xyz, shells, f"water{n}_qz_s{seed}", seed)
+
+
 def random_shells_molecule(ls, seed: int, nprim=(1, 3), exp_range=(0.2, 3.0),
                            box: float = 1.5, coef_range=(0.2, 1.0),
                            Z=None) -> Molecule:
