@@ -1003,6 +1003,14 @@ def rys_water_qz(steps=10, warmup=3, cluster=8):
         e1.record(st)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
+    # analytic RHF gradient (forces) at the converged density; the first call
+    # builds the derivative lists, the second is timed
+    basis.gradient(r)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grad = basis.gradient(r)
+    torch.cuda.synchronize()
+    grad_s = time.perf_counter() - t0
     prof = basis.fock_jk_profiled(D, J, K, o)
     stats = basis.class_stats(o)
     rys_ms = rys_flops = 0.0
@@ -1024,6 +1032,8 @@ def rys_water_qz(steps=10, warmup=3, cluster=8):
            "nbf": int(basis.nbf), "scf_s": scf_s, "scf_iterations": int(r.iterations),
            "energy": r.energy, "abs_dE_vs_oracle": abs(r.energy - ref["energy"]),
            "jk_ms": statistics.median(ms), "builds_per_s": 1000.0 / statistics.median(ms),
+           "gradient_s": grad_s, "gradient_max_abs": float(np.abs(grad).max()),
+           "gradient_sum_abs": float(np.abs(grad.sum(axis=0)).max()),
            "class_ms_serial_total": float(prof.sum()), "rys_class_ms_serial": rys_ms,
            "rys_share_serial": rys_ms / float(prof.sum()) if prof.sum() > 0 else 0.0,
            "roofline_rys": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,

@@ -353,6 +353,27 @@ int hf_uhf_solve(hf_basis* b, int n_alpha, int n_beta, const hf_scf_opts* opts, 
  * HF_ERR_OOM, HF_ERR_CUDA. */
 int hf_mp2_energy(hf_basis* b, const double* C, const double* eps, int n_occ, double* e2);
 
+/* ---------------------------------------------------------------- forces */
+
+/* Analytic nuclear gradient dE/dR (natom x 3, Eh/bohr) of the converged
+ * closed-shell RHF energy; the paper's Hartree-Fock interatomic forces are
+ * its negative.  With D = C_occ C_occ^T and W = C_occ diag(eps_occ)
+ * C_occ^T:
+ *   dE/dR = 2 sum D dH/dR - 2 sum W dS/dR
+ *         + sum_(ijkl) (2 D_ij D_kl - D_ik D_jl) d(ij|kl)/dR + dE_nuc/dR,
+ * the derivative integrals of Eq. 5 by Rys quadrature (every class), those
+ * of Eqs. 2-4 by Obara-Saika (overlap, kinetic) and Rys quadrature
+ * (nuclear attraction, including the derivative of the operator's centre).
+ * C: nbf x nbf DEVICE, row-major, C[mu][p] (as hf_scf_result.C); eps: nbf
+ * orbital energies, ascending, DEVICE; n_occ occupied orbitals (nelec / 2);
+ * opts: Schwarz tau of the derivative quartets (NULL = defaults;
+ * HF_JK_HOST and HF_JK_DETERMINISTIC are rejected).  grad: natom x 3 HOST
+ * doubles, overwritten.  The call allocates O(nbf^2) device scratch and
+ * leaves the basis's work lists in their Rys shape.  Errors:
+ * HF_ERR_INVALID, HF_ERR_OOM, HF_ERR_CUDA. */
+int hf_rhf_gradient(hf_basis* b, const double* C, const double* eps, int n_occ, const hf_jk_opts* opts,
+                    double* grad);
+
 /* ---------------------------------------------------------------- Rys rule */
 
 /* The n-point Rys quadrature rule at T (Eq. 5 evaluated by Rys quadrature):

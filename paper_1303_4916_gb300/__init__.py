@@ -19,6 +19,7 @@ from .api import (  # noqa: F401
     hf_jk_stored,
     hf_mp2_energy,
     hf_one_electron,
+    hf_rhf_gradient,
     hf_rys_rule,
     hf_scf_solve,
     hf_scf_solve_batch,

@@ -137,6 +137,7 @@ SIGNATURES = {
     "hf_uhf_solve": (I, [P, I, I, C.POINTER(hf_scf_opts), C.POINTER(hf_uhf_result)]),
     "hf_mp2_energy": (I, [P, P, P, I, C.POINTER(D)]),
     "hf_rys_rule": (I, [I, D, C.POINTER(D), C.POINTER(D)]),
+    "hf_rhf_gradient": (I, [P, P, P, I, P, C.POINTER(D)]),
     "hf_scf_solve_batch": (I, [C.POINTER(P), I, C.POINTER(hf_scf_opts), C.POINTER(hf_scf_result),
                                C.POINTER(I)]),
     "hf_serve_opts_default": (None, [C.POINTER(hf_serve_opts)]),

@@ -155,6 +155,7 @@ class Basis:
         self.nbf = lib.hf_basis_nbf(self._h)
         self.nshell = lib.hf_basis_nshell(self._h)
         self.n_electrons = ne
+        self.natom = len(atoms)
 
     @property
     def handle(self):
@@ -279,6 +280,18 @@ class Basis:
         e2 = C.c_double()
         _check(_lib().hf_mp2_energy(self._h, _ptr(Cmo), _ptr(eps), int(n_occ), C.byref(e2)), "hf_mp2_energy")
         return float(e2.value)
+
+    def gradient(self, scf_result=None, schwarz_tau: float = 1e-12, e_tol: float = 1e-11):
+        """Analytic RHF gradient dE/dR (numpy natom x 3, Eh/bohr) at the
+        converged density of scf_result (a tight SCF is run when none is
+        given); the forces are its negative."""
+        r = scf_result if scf_result is not None else self.scf(e_tol=e_tol, schwarz_tau=schwarz_tau)
+        g = np.zeros((self.natom, 3))
+        o = jk_opts(schwarz_tau)
+        _check(_lib().hf_rhf_gradient(self._h, _ptr(r.tensors["C"]), _ptr(r.tensors["eps"]),
+                                      int(self.n_electrons // 2), C.byref(o),
+                                      g.ctypes.data_as(C.POINTER(C.c_double))), "hf_rhf_gradient")
+        return g
 
     def fock_jk_uhf(self, Da, Db, opts: Optional[hf_jk_opts] = None):
         """J[Da + Db], K[Da], K[Db] (CUDA tensors) from one integral evaluation."""
@@ -486,6 +499,10 @@ def hf_fock_jk_uhf(basis: Basis, Da, Db, opts: Optional[hf_jk_opts] = None):
 
 def hf_mp2_energy(basis: Basis, C_mo, eps, n_occ: int) -> float:
     return basis.mp2_energy(C_mo, eps, n_occ)
+
+
+def hf_rhf_gradient(basis: Basis, scf_result=None, schwarz_tau: float = 1e-12):
+    return basis.gradient(scf_result, schwarz_tau)
 
 
 def hf_scf_solve_batch(bases, **kw):

@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libhf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # heaviest first, so the long compiles start early
 SOURCES = ["eri_d6.cu", "eri_d5.cu", "eri_d4.cu", "eri_d3.cu", "eri_d2.cu", "eri_d1.cu", "eri_sp.cu",
-           "rys.cu", "api.cu", "basis.cu", "onee.cu", "scf.cu", "batch.cu", "serve.cu", "noalloc.cu", "multi.cu",
+           "rys.cu", "grad.cu", "api.cu", "basis.cu", "onee.cu", "scf.cu", "batch.cu", "serve.cu", "noalloc.cu", "multi.cu",
            "mp2.cu"]
 KERNEL_HEADERS = ["eri.cuh", "eri_classes.cuh", "hf_device.h"]
 HEADERS = KERNEL_HEADERS + ["rys.cuh", "hf_internal.h", "scf_internal.h", "multi.h", "../../include/hf.h"]

@@ -27,7 +27,8 @@ static int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 // ------------------------------------------------------------- pair kernel
 // One thread per shell pair (A, B), l_A >= l_B: for each primitive pair
 // p = a + b, P = (a A + b B)/p, PA = P - A and
-// K = c_a c_b exp(-ab/p |AB|^2) sqrt(2) pi^(5/4) / p; records are sorted by
+// K = c_a c_b exp(-ab/p |AB|^2) sqrt(2) pi^(5/4) / p and the exponent a of
+// A's primitive (the derivative integrals need it); records are sorted by
 // the magnitude bound |K| (2p)^(-1/4) (1 + |AB| + p^(-1/2))^(l_A+l_B) and
 // those below kPrimEps are not counted.
 __global__ void pair_kernel(int npairs, const int* __restrict__ pA, const int* __restrict__ pB,
@@ -78,7 +79,7 @@ __global__ void pair_kernel(int npairs, const int* __restrict__ pA, const int* _
     const double Px = (a * Ax + b * Bx) / p, Py = (a * Ay + b * By) / p, Pz = (a * Az + b * Bz) / p;
     double* r = prim64 + (size_t)(base + s) * PRIM64_STRIDE;
     r[0] = p; r[1] = 0.5 / p; r[2] = Px; r[3] = Py; r[4] = Pz;
-    r[5] = Px - Ax; r[6] = Py - Ay; r[7] = Pz - Az; r[8] = K; r[9] = 0.0;
+    r[5] = Px - Ax; r[6] = Py - Ay; r[7] = Pz - Az; r[8] = K; r[9] = a;
     float* f = prim32 + (size_t)(base + s) * PRIM32_STRIDE;
     for (int x = 0; x < 10; ++x) f[x] = (float)r[x];
     f[10] = 0.f; f[11] = 0.f;

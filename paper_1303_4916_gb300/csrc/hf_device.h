@@ -30,9 +30,10 @@
 // generic cooperative kernel
 #define HF_DF_LMAX 4
 
-// Primitive-pair record, FP64: p, 1/(2p), P[3], PA[3], K, pad (80 bytes);
-// FP32: the same nine values then three pads (48 bytes); df64: the nine
-// values as (hi, lo) float pairs then one pad pair (80 bytes).
+// Primitive-pair record, FP64: p, 1/(2p), P[3], PA[3], K, a (80 bytes; a
+// is the exponent of A's primitive, b = p - a); FP32: the same ten values
+// then two pads (48 bytes); df64: the ten values as (hi, lo) float pairs
+// (80 bytes).
 // K = c_a c_b exp(-ab/p |AB|^2) sqrt(2) pi^(5/4) / p, so that the
 // primitive-quartet prefactor 2 pi^(5/2) / (p q sqrt(p+q)) K_ab K_cd of
 // [00|00]^(m) is K_ab' K_cd' / sqrt(p+q).
@@ -154,6 +155,11 @@ typedef void (*jk_launch_fn)(const JKWork&, const PairSet&, const KernelCommon&,
 typedef void (*store_launch_fn)(const JKWork&, const PairSet&, const KernelCommon&, double*, int, int, cudaStream_t);
 typedef void (*schwarz_launch_fn)(const int*, int, const PairSet&, const KernelCommon&, double*, cudaStream_t);
 typedef int (*occ_fn)();
+// Nuclear-gradient launch of one class: the class's Rys work list, the
+// density D (nbf x nbf), the atom of every basis function, and the
+// gradient accumulator (natom x 3).
+typedef void (*grad_launch_fn)(const JKWork&, const PairSet&, const KernelCommon&, const double* D,
+                               const int* bf_atom, int nbf, double* grad, int grid, cudaStream_t);
 
 struct EriClassOps {
   jk_launch_fn jk64;
@@ -166,6 +172,7 @@ struct EriClassOps {
   occ_fn occ32;
   occ_fn occdf;
   occ_fn occrys;
+  grad_launch_fn grad;  // derivative ERIs contracted for the RHF gradient (Rys route, every class)
   int chunk;      // kets per work item: 32 (warp of quartets) or 1 (warp-cooperative class)
   int rys_nchunks;  // output chunks per quartet of the Rys kernel (every class)
   int rys_native;   // the class has an f or g shell: only the Rys kernel serves it

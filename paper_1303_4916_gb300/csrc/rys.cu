@@ -790,6 +790,237 @@ __global__ void __launch_bounds__(128) rys_schwarz_kernel(const int* __restrict_
   if (lane == 0) Q[pid] = sqrt(m);
 }
 
+// ------------------------------------------------------------- nuclear gradient
+// Derivative integrals for the analytic RHF gradient.  A primitive's
+// derivative with respect to its centre is d/dA_x [x_A^a e^(-alpha x_A^2)]
+// = 2 alpha x_A^(a+1) e - a x_A^(a-1) e, so per direction the one-dimensional
+// factor of (ab|cd) with respect to A becomes 2 alpha I(a+1, b, c, d) -
+// a I(a-1, b, c, d) (likewise b, beta for B and c, gamma for C); D follows
+// by translational invariance, dD = -(dA + dB + dC).  The tables are one
+// power higher on A, B and C than the energy's.  Each warp contracts its
+// quartet's derivative integrals on the fly with
+//     Gamma = 8 w [2 D_ab D_cd - (D_ac D_bd + D_ad D_bc) / 2]
+// (w the symmetry weight of the unique quartet), the two-electron part of
+// dE/dR = sum over unique quartets of Gamma d(ab|cd)/dR with the energy
+// E_2e = 2 Tr[D J] - Tr[D K].
+struct GradClass {
+  RysClass base;        // the J/K class: chunks and work-list shape
+  int n;                // roots (total angular momentum + 1)
+  int NG, MG;           // highest G powers: la + lb + 1, lc + ld + 1
+  int SG, SH, SI;       // per-direction table sizes
+  int oG, oH, oI, oX;   // offsets in the warp slice (doubles); oX: per-output table
+  int ws;
+};
+
+inline GradClass grad_class(const RysClass& rc) {
+  GradClass g{};
+  g.base = rc;
+  g.n = (rc.la + rc.lb + rc.lc + rc.ld + 1) / 2 + 1;
+  g.NG = rc.nmax + 1;
+  g.MG = rc.mmax + 1;
+  g.SG = (g.NG + 1) * (g.MG + 1);
+  g.SH = (rc.la + 2) * (rc.lb + 2) * (g.MG + 1);
+  g.SI = (rc.la + 2) * (rc.lb + 2) * (rc.lc + 2) * (rc.ld + 1);
+  g.oG = kHead;
+  g.oH = g.oG + 3 * g.SG;
+  int end = g.oH + 3 * g.SH;
+  g.oI = rc.ld == 0 ? g.oH : end;  // ld = 0: I is H (ic = m)
+  if (rc.ld > 0) end = g.oI + 3 * g.SI;
+  g.oX = (end + 1) & ~1;
+  g.ws = g.oX + 3 * rc.rpc * rc.nc * rc.nd;
+  g.ws = (g.ws + 1) & ~1;
+  return g;
+}
+
+__global__ void __launch_bounds__(128) rys_grad_kernel(const JKWork w, const PairSet ps, const KernelCommon kc,
+                                                       const double* __restrict__ D,
+                                                       const int* __restrict__ bf_atom, int nbf,
+                                                       double* __restrict__ grad, const GradClass gc) {
+  extern __shared__ __align__(16) double rsm[];
+  const RysClass& rc = gc.base;
+  double* const s = rsm + (threadIdx.x >> 5) * gc.ws;
+  const int lane = threadIdx.x & 31;
+  const int NB = rc.nb, NC = rc.nc, ND = rc.nd, NCD = NC * ND;
+  const int lb2 = rc.lb + 2, lc2 = rc.lc + 2, ld1 = rc.ld + 1;
+  const int sC = ld1, sB = lc2 * ld1, sA = lb2 * lc2 * ld1;
+  const int L1 = gc.NG + 1, M1 = gc.MG + 1;
+  const bool gl = lane < 3 * L1;
+  const int gdir = gl ? lane / L1 : 0, gn = gl ? lane - gdir * L1 : 0;
+  double* const ru = s + kRu;
+  double* const rw = s + kRw;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(w.counter, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= w.nitems) break;
+    ItemRange it;
+    rys_item(w, t, &it);
+    const int bp = __ldg(w.bra + it.bi);
+    if (!HF_BCHECK(kc, bp >= 0 && bp < ps.npairs, HF_BC_PAIR, bp)) continue;
+    const PairInfo bra = ps.info[bp];
+    for (int kidx = it.k0; kidx < it.k1; ++kidx) {
+      const int kp = __ldg(w.ket + kidx);
+      if (!HF_BCHECK(kc, kp >= 0 && kp < ps.npairs, HF_BC_PAIR, kp)) continue;
+      const PairInfo ket = ps.info[kp];
+      int q_lo, q_hi, c_lo, c_hi;
+      rys_part(rc, w, bra, ket, it.part, it.nsp, &q_lo, &q_hi, &c_lo, &c_hi);
+      if (q_hi <= q_lo) continue;
+      rys_setup(rc, bra.AB, ket.AB, s, lane);
+      double wdeg = 8.0;
+      if (bra.same) wdeg *= 0.5;
+      if (ket.same) wdeg *= 0.5;
+      if (bp == kp) wdeg *= 0.5;
+      const int a0 = bra.bfA, b0 = bra.bfB, c0 = ket.bfA, d0 = ket.bfB;
+      double g[9];  // dE/dA, dE/dB, dE/dC (x, y, z each)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) g[k] = 0.0;
+      for (int ch = c_lo; ch < c_hi; ++ch) {
+        const int r0 = ch * rc.rpc, r1 = min(r0 + rc.rpc, rc.na * NB);
+        const int nout = (r1 - r0) * NCD;
+        __syncwarp();
+        // per output: Gamma (scaled), table offsets, Cartesian powers
+        double* X = s + gc.oX;
+        for (int e = lane; e < nout; e += 32) {
+          const int rl = e / NCD, cd = e - rl * NCD;
+          const int row = r0 + rl, a = row / NB, b = row - a * NB;
+          const int c = cd / ND, d = cd - c * ND;
+          const int pa = cart(rc.la, a), pb = cart(rc.lb, b), pc = cart(rc.lc, c), pd = cart(rc.ld, d);
+          auto off = [&](int sh) {
+            return ((((pa >> sh) & 15) * lb2 + ((pb >> sh) & 15)) * lc2 + ((pc >> sh) & 15)) * ld1 + ((pd >> sh) & 15);
+          };
+          auto Dv = [&](int i, int j) { return __ldg(D + (size_t)i * nbf + j); };
+          const int ia = a0 + a, ib = b0 + b, ic = c0 + c, id = d0 + d;
+          const double gam = wdeg * s[kSc + a] * s[kSc + 21 + b] * s[kSc + 42 + c] * s[kSc + 63 + d] *
+                             (2.0 * Dv(ia, ib) * Dv(ic, id) - 0.5 * (Dv(ia, ic) * Dv(ib, id) + Dv(ia, id) * Dv(ib, ic)));
+          const long long idx = (long long)off(0) | ((long long)off(4) << 21) | ((long long)off(8) << 42);
+          const long long pw = (long long)(pa & 0xfff) | ((long long)(pb & 0xfff) << 12) | ((long long)(pc & 0xfff) << 24);
+          X[3 * e] = gam;
+          X[3 * e + 1] = __longlong_as_double(idx);
+          X[3 * e + 2] = __longlong_as_double(pw);
+        }
+        __syncwarp();
+        const int nk = ket.nprim;
+        for (int qq = q_lo; qq < q_hi; ++qq) {
+          const int ibp = qq / nk, ikp = qq - ibp * nk;
+          const double* rb = ps.prim64 + (size_t)(bra.prim0 + ibp) * PRIM64_STRIDE;
+          const double* rk = ps.prim64 + (size_t)(ket.prim0 + ikp) * PRIM64_STRIDE;
+          const double p = __ldg(rb), q = __ldg(rk);
+          const double PQx = __ldg(rb + 2) - __ldg(rk + 2), PQy = __ldg(rb + 3) - __ldg(rk + 3),
+                       PQz = __ldg(rb + 4) - __ldg(rk + 4);
+          const double ipq = 1.0 / (p + q);
+          const double T = p * q * ipq * (PQx * PQx + PQy * PQy + PQz * PQz);
+          const double pref = __ldg(rb + 8) * __ldg(rk + 8) * sqrt(ipq);
+          const double za2 = 2.0 * __ldg(rb + 9), zb2 = 2.0 * (p - __ldg(rb + 9)), zc2 = 2.0 * __ldg(rk + 9);
+          if (lane < gc.n) rys_rule_root(kc.rys, gc.n, lane, T, ru + lane, rw + lane);
+          const double qf = q * ipq, pf = p * ipq;
+          const double PQg = gdir == 0 ? PQx : (gdir == 1 ? PQy : PQz);
+          const double PAg = __ldg(rb + 5 + gdir), QCg = __ldg(rk + 5 + gdir);
+          const double hp = __ldg(rb + 1), hq = __ldg(rk + 1);
+          __syncwarp();
+          for (int r = 0; r < gc.n; ++r) {
+            const double u = ru[r];
+            const double B00 = 0.5 * u * ipq, B10 = hp * (1.0 - u * qf), B01 = hq * (1.0 - u * pf);
+            {
+              const double c00 = PAg - u * qf * PQg, d00 = QCg + u * pf * PQg;
+              double gg = gdir == 2 ? rw[r] * pref : 1.0, gp = 0.0;
+              for (int k = 0; k < gn; ++k) {
+                const double tt = c00 * gg + k * B10 * gp;
+                gp = gg;
+                gg = tt;
+              }
+              double* Gd = s + gc.oG + gdir * gc.SG + gn * M1;
+              if (gl) Gd[0] = gg;
+              double gm = 0.0;
+              for (int m = 0; m < gc.MG; ++m) {
+                const double left = __shfl_up_sync(0xffffffffu, gg, 1);
+                const double tt = d00 * gg + m * B01 * gm + (gn > 0 ? gn * B00 * left : 0.0);
+                gm = gg;
+                gg = tt;
+                if (gl) Gd[m + 1] = gg;
+              }
+            }
+            __syncwarp();
+            {  // H(ia, ib, m), ia <= la + 1, ib <= lb + 1
+              Radix wk(lane, rc.la + 2, lb2, M1);
+              for (int e = lane; e < 3 * gc.SH; e += 32, wk.step()) {
+                const int dir = wk.d[0], ia = wk.d[1], ib2 = wk.d[2], m = wk.d[3];
+                const double* gp2 = s + gc.oG + dir * gc.SG + ia * M1 + m;
+                const double* cf = s + kCb + (dir * 6 + ib2) * 6;
+                double v = 0.0;
+                if (ia + ib2 <= gc.NG)
+                  for (int k = 0; k <= ib2; ++k) v = fma(cf[k], gp2[k * M1], v);
+                s[gc.oH + e] = v;
+              }
+              __syncwarp();
+            }
+            if (rc.ld > 0) {  // I(iab, ic, id), ic <= lc + 1, id <= ld
+              Radix wk(lane, (rc.la + 2) * lb2, lc2, ld1);
+              for (int e = lane; e < 3 * gc.SI; e += 32, wk.step()) {
+                const int dir = wk.d[0], iab = wk.d[1], ic = wk.d[2], id = wk.d[3];
+                const double* h = s + gc.oH + dir * gc.SH + iab * M1 + ic;
+                const double* cf = s + kCd + (dir * 6 + id) * 6;
+                double v = 0.0;
+                if (ic + id <= gc.MG)
+                  for (int k = 0; k <= id; ++k) v = fma(cf[k], h[k], v);
+                s[gc.oI + e] = v;
+              }
+              __syncwarp();
+            }
+            const double* Ix = s + gc.oI;
+            const double* Iy = Ix + gc.SI;
+            const double* Iz = Iy + gc.SI;
+            for (int e = lane; e < nout; e += 32) {
+              const double gam = X[3 * e];
+              const long long idx = __double_as_longlong(X[3 * e + 1]);
+              const long long pw = __double_as_longlong(X[3 * e + 2]);
+              const int o3[3] = {(int)(idx & 0x1fffff), (int)((idx >> 21) & 0x1fffff), (int)(idx >> 42)};
+              const double* I3[3] = {Ix, Iy, Iz};
+              double v0[3], vA[3], vB[3], vC[3];
+#pragma unroll
+              for (int dd = 0; dd < 3; ++dd) {
+                const double* Id = I3[dd];
+                const int o = o3[dd];
+                const int na_ = (int)((pw >> (4 * dd)) & 15), nb_ = (int)((pw >> (12 + 4 * dd)) & 15),
+                          nc_ = (int)((pw >> (24 + 4 * dd)) & 15);
+                v0[dd] = Id[o];
+                vA[dd] = za2 * Id[o + sA] - (na_ > 0 ? na_ * Id[o - sA] : 0.0);
+                vB[dd] = zb2 * Id[o + sB] - (nb_ > 0 ? nb_ * Id[o - sB] : 0.0);
+                vC[dd] = zc2 * Id[o + sC] - (nc_ > 0 ? nc_ * Id[o - sC] : 0.0);
+              }
+              const double yz = v0[1] * v0[2], xz = v0[0] * v0[2], xy = v0[0] * v0[1];
+              g[0] = fma(gam, vA[0] * yz, g[0]);
+              g[1] = fma(gam, vA[1] * xz, g[1]);
+              g[2] = fma(gam, vA[2] * xy, g[2]);
+              g[3] = fma(gam, vB[0] * yz, g[3]);
+              g[4] = fma(gam, vB[1] * xz, g[4]);
+              g[5] = fma(gam, vB[2] * xy, g[5]);
+              g[6] = fma(gam, vC[0] * yz, g[6]);
+              g[7] = fma(gam, vC[1] * xz, g[7]);
+              g[8] = fma(gam, vC[2] * xy, g[8]);
+            }
+            __syncwarp();
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g[k] += __shfl_xor_sync(0xffffffffu, g[k], o);
+      if (lane == 0) {
+        const int at[3] = {__ldg(bf_atom + a0), __ldg(bf_atom + b0), __ldg(bf_atom + c0)};
+        const int atD = __ldg(bf_atom + d0);
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          atomicAdd(grad + 3 * at[0] + x, g[x]);
+          atomicAdd(grad + 3 * at[1] + x, g[3 + x]);
+          atomicAdd(grad + 3 * at[2] + x, g[6 + x]);
+          atomicAdd(grad + 3 * atD + x, -(g[x] + g[3 + x] + g[6 + x]));
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------- launchers
 size_t smem_of(const RysClass& rc, int warps) { return (size_t)warps * rc.ws * sizeof(double); }
 
@@ -859,6 +1090,21 @@ void schwarz_launch(const int* pairs, int npairs, const PairSet& ps, const Kerne
 #undef RYS_Q
 }
 
+template <int CLS>
+void grad_launch(const JKWork& w, const PairSet& ps, const KernelCommon& kc, const double* D, const int* bf_atom,
+                 int nbf, double* grad, int grid, cudaStream_t st) {
+  static const GradClass gc = grad_class(rys_class_of(CLS));
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(rys_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  // four warps per block where their slices fit in 227 KB, else two
+  const int warps = 4 * gc.ws * (int)sizeof(double) <= 227 * 1024 ? 4 : 2;
+  const int blocks = std::max(1, std::min(grid, (w.nitems + warps - 1) / warps));
+  rys_grad_kernel<<<blocks, 32 * warps, (size_t)warps * gc.ws * sizeof(double), st>>>(w, ps, kc, D, bf_atom, nbf,
+                                                                                       grad, gc);
+}
+
 template <size_t... I>
 void register_all(EriClassOps* table, std::index_sequence<I...>) {
   static const char* const kL = "spdfg";
@@ -867,10 +1113,12 @@ void register_all(EriClassOps* table, std::index_sequence<I...>) {
   const occ_fn occ[] = {&jk_occ<(int)I>...};
   const store_launch_fn store[] = {&store_launch<(int)I>...};
   const schwarz_launch_fn schw[] = {&schwarz_launch<(int)I>...};
+  const grad_launch_fn grd[] = {&grad_launch<(int)I>...};
   for (int c = 0; c < HF_NCLASS; ++c) {
     EriClassOps& e = table[c];
     e.jkrys = jk[c];
     e.occrys = occ[c];
+    e.grad = grd[c];
     const RysClass rc = rys_class_of(c);
     e.rys_nchunks = rc.nchunks;
     e.rys_native = rc.native;

@@ -9,6 +9,7 @@ oracle under ``oracle/`` and the CUDA library), each with its own code.
 from .molecules import (  # noqa: F401
     water_qz,
     water_cluster_qz,
+    small_f_molecule,
     Molecule,
     h_line,
     lattice_molecule,
