@@ -21,7 +21,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # heaviest first, so the long compiles start early
-SOURCES = ["eri_d6.cu", "eri_d5.cu", "eri_d4.cu", "eri_d3.cu", "eri_d2.cu", "eri_d1.cu", "eri_sp.cu",
+SOURCES = ["rys_thread.cu", "eri_d6.cu", "eri_d5.cu", "eri_d4.cu", "eri_d3.cu", "eri_d2.cu", "eri_d1.cu", "eri_sp.cu",
            "rys.cu", "grad.cu", "api.cu", "basis.cu", "onee.cu", "scf.cu", "batch.cu", "serve.cu", "noalloc.cu", "multi.cu",
            "mp2.cu"]
 KERNEL_HEADERS = ["eri.cuh", "eri_classes.cuh", "hf_device.h"]

@@ -434,7 +434,7 @@ int hf_basis_prepare_work(hf_basis* b, double tau, double fp32_bound, unsigned f
       const std::vector<int>& bk = b->buckets[Y];
       // Rys lists (f/g classes, or every class under HF_JK_RYS): one ket
       // per item, each item split into the class's output chunks
-      const bool rys_list = rys || ctx->ops[cls].rys_native;
+      const bool rys_list = rys || (ctx->ops[cls].rys_native && ctx->ops[cls].chunk == 1);
       const int chunk = rys_list ? 1 : ctx->ops[cls].chunk;
       const int nchunk = rys_list ? ctx->ops[cls].rys_nchunks : 0;
       std::vector<int> bra[2], kb[2], ke[2], io[2], sp[2];

@@ -27,6 +27,7 @@
 #include "df64.cuh"
 #include "eri_classes.cuh"
 #include "hf_device.h"
+#include "rys.cuh"
 
 namespace hfk {
 
@@ -341,10 +342,137 @@ __device__ __forceinline__ void contracted_vrr_df(const PairSet& ps, const Kerne
   }
 }
 
-// Cartesian component scale of a d function relative to the axial one
-// (xy, xz, yz carry sqrt(3)); s and p components are 1.
+// Cartesian component scale relative to the axial component,
+// sqrt((2l-1)!! / ((2x-1)!! (2y-1)!! (2z-1)!!)), components ordered x power
+// descending then y: d xy, xz, yz carry sqrt(3); f xyz sqrt(15), the
+// mixed ones sqrt(5); g x^2yz-type sqrt(35), x^2y^2-type sqrt(35/3),
+// x^3y-type sqrt(7); s, p and the axial components 1.
 __device__ __forceinline__ constexpr double comp_scale(int l, int c) {
-  return (l == 2 && (c == 1 || c == 2 || c == 4)) ? 1.7320508075688772935 : 1.0;
+  return l == 2   ? ((c == 1 || c == 2 || c == 4) ? 1.7320508075688772935 : 1.0)
+         : l == 3 ? (c == 4 ? 3.8729833462074168852 : (c == 0 || c == 6 || c == 9) ? 1.0 : 2.2360679774997896964)
+         : l == 4 ? ((c == 0 || c == 10 || c == 14)  ? 1.0
+                     : (c == 4 || c == 7 || c == 8)  ? 5.9160797830996160426
+                     : (c == 3 || c == 5 || c == 12) ? 3.4156502553198660478
+                                                     : 2.6457513110645905905)
+                  : 1.0;
+}
+
+// Classes evaluated by Rys quadrature in the thread-per-quartet kernel
+// declare RYS = true (rys.cu); the generated classes do not.
+template <class C, class = void>
+struct IsRys : std::false_type {};
+template <class C>
+struct IsRys<C, std::void_t<decltype(C::RYS)>> : std::integral_constant<bool, C::RYS> {};
+
+__host__ __device__ constexpr int cart_power(int l, int c, int dir) {
+  int k = 0;
+  for (int x = l; x >= 0; --x)
+    for (int y = l - x; y >= 0; --y) {
+      if (k == c) return dir == 0 ? x : (dir == 1 ? y : l - x - y);
+      ++k;
+    }
+  return 0;
+}
+__host__ __device__ constexpr double binom_c(int n, int k) {
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+// Contracted block of a small class by Rys quadrature, one quartet per lane
+// (the recurrences of rys.cu with every size known at compile time, so the
+// tables stay in registers): over the bra primitive pairs [ib0, ib1) and
+// all ket primitives, per root the three G(n, m) tables, the transfer to
+// B and D, and the Ix Iy Iz products, into I[(a NB + b) NC ND + c ND + d]
+// (component scales not applied).  Inactive lanes return zeros.
+template <class C>
+__device__ __forceinline__ void rys_thread_block(const PairSet& P, const KernelCommon& kc, const PairInfo& bra,
+                                                 const PairInfo& ket, int ib0, int ib1, bool active, double* I) {
+  constexpr int LA = C::LA, LB = C::LB, LC = C::LC, LD = C::LD;
+  constexpr int NA = C::NA, NB = C::NB, NC = C::NC, ND = C::ND;
+  constexpr int NMAX = LA + LB, MMAX = LC + LD, NR = (LA + LB + LC + LD) / 2 + 1;
+  constexpr int S4 = (LA + 1) * (LB + 1) * (LC + 1) * (LD + 1);
+#pragma unroll
+  for (int o = 0; o < NA * NB * NC * ND; ++o) I[o] = 0.0;
+  if (!active) return;
+  double ABp[3][LB + 1], CDp[3][LD + 1];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    ABp[d][0] = 1.0;
+    CDp[d][0] = 1.0;
+#pragma unroll
+    for (int k = 1; k <= LB; ++k) ABp[d][k] = ABp[d][k - 1] * bra.AB[d];
+#pragma unroll
+    for (int k = 1; k <= LD; ++k) CDp[d][k] = CDp[d][k - 1] * ket.AB[d];
+  }
+  const int nk = ket.nprim;
+  for (int ib = ib0; ib < ib1; ++ib) {
+    const double* rb = P.prim64 + (size_t)(bra.prim0 + ib) * PRIM64_STRIDE;
+    const double p = __ldg(rb), hp = __ldg(rb + 1);
+    const double Pp[3] = {__ldg(rb + 2), __ldg(rb + 3), __ldg(rb + 4)};
+    const double PA[3] = {__ldg(rb + 5), __ldg(rb + 6), __ldg(rb + 7)};
+    const double Kab = __ldg(rb + 8);
+    for (int ik = 0; ik < nk; ++ik) {
+      const double* rk = P.prim64 + (size_t)(ket.prim0 + ik) * PRIM64_STRIDE;
+      const double q = __ldg(rk), hq = __ldg(rk + 1);
+      const double PQ[3] = {Pp[0] - __ldg(rk + 2), Pp[1] - __ldg(rk + 3), Pp[2] - __ldg(rk + 4)};
+      const double QC[3] = {__ldg(rk + 5), __ldg(rk + 6), __ldg(rk + 7)};
+      const double ipq = 1.0 / (p + q);
+      const double T = p * q * ipq * (PQ[0] * PQ[0] + PQ[1] * PQ[1] + PQ[2] * PQ[2]);
+      const double pref = Kab * __ldg(rk + 8) * sqrt(ipq);
+      const double qf = q * ipq, pf = p * ipq;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        double u, w;
+        rys_rule_root(kc.rys, NR, r, T, &u, &w);
+        const double B00 = 0.5 * u * ipq, B10 = hp * (1.0 - u * qf), B01 = hq * (1.0 - u * pf);
+        double X[3][S4];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          double G[NMAX + 1][MMAX + 1];
+          const double c00 = PA[d] - u * qf * PQ[d], d00 = QC[d] + u * pf * PQ[d];
+          G[0][0] = d == 2 ? w * pref : 1.0;
+#pragma unroll
+          for (int n = 0; n < NMAX; ++n) G[n + 1][0] = c00 * G[n][0] + (n > 0 ? n * B10 * G[n - 1][0] : 0.0);
+#pragma unroll
+          for (int m = 0; m < MMAX; ++m)
+#pragma unroll
+            for (int n = 0; n <= NMAX; ++n)
+              G[n][m + 1] = d00 * G[n][m] + (m > 0 ? m * B01 * G[n][m - 1] : 0.0) + (n > 0 ? n * B00 * G[n - 1][m] : 0.0);
+#pragma unroll
+          for (int ia = 0; ia <= LA; ++ia)
+#pragma unroll
+            for (int jb = 0; jb <= LB; ++jb)
+#pragma unroll
+              for (int ic = 0; ic <= LC; ++ic)
+#pragma unroll
+                for (int jd = 0; jd <= LD; ++jd) {
+                  double v = 0.0;
+#pragma unroll
+                  for (int k = 0; k <= jb; ++k)
+#pragma unroll
+                    for (int l = 0; l <= jd; ++l)
+                      v += binom_c(jb, k) * binom_c(jd, l) * ABp[d][jb - k] * CDp[d][jd - l] * G[ia + k][ic + l];
+                  X[d][((ia * (LB + 1) + jb) * (LC + 1) + ic) * (LD + 1) + jd] = v;
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+              for (int dd = 0; dd < ND; ++dd) {
+                const int o = ((a * NB + b) * NC + c) * ND + dd;
+                const int ix = ((cart_power(LA, a, 0) * (LB + 1) + cart_power(LB, b, 0)) * (LC + 1) + cart_power(LC, c, 0)) * (LD + 1) + cart_power(LD, dd, 0);
+                const int iy = ((cart_power(LA, a, 1) * (LB + 1) + cart_power(LB, b, 1)) * (LC + 1) + cart_power(LC, c, 1)) * (LD + 1) + cart_power(LD, dd, 1);
+                const int iz = ((cart_power(LA, a, 2) * (LB + 1) + cart_power(LB, b, 2)) * (LC + 1) + cart_power(LC, c, 2)) * (LD + 1) + cart_power(LD, dd, 2);
+                I[o] = fma(X[0][ix] * X[1][iy], X[2][iz], I[o]);
+              }
+      }
+    }
+  }
 }
 
 // One contribution v to element idx of an accumulator.  Default: an FP64
@@ -437,13 +565,16 @@ __global__ void __launch_bounds__(128) eri_jk_kernel(const JKWork w, const PairS
     // the contraction is linear, so the parts' digested blocks add up)
     const int ib0 = part * bra.nprim / nsp, ib1 = (part + 1) * bra.nprim / nsp;
 
-    R acc[C::NE * C::NF];
-    if constexpr (std::is_same<R, df64>::value)
-      contracted_vrr_df<C>(P, kc, bra.prim0 + ib0, ib1 - ib0, ket.prim0, active ? ket.nprim : 0, acc);
-    else
-      contracted_vrr<C, R>(P, kc, bra.prim0 + ib0, ib1 - ib0, ket.prim0, active ? ket.nprim : 0, acc);
     R I[NA * NB * NC * ND];
-    {
+    if constexpr (IsRys<C>::value) {
+      static_assert(std::is_same<R, double>::value, "Rys thread classes run in FP64");
+      rys_thread_block<C>(P, kc, bra, ket, ib0, ib1, active, I);
+    } else {
+      R acc[C::NE * C::NF];
+      if constexpr (std::is_same<R, df64>::value)
+        contracted_vrr_df<C>(P, kc, bra.prim0 + ib0, ib1 - ib0, ket.prim0, active ? ket.nprim : 0, acc);
+      else
+        contracted_vrr<C, R>(P, kc, bra.prim0 + ib0, ib1 - ib0, ket.prim0, active ? ket.nprim : 0, acc);
       R AB[3] = {(R)bra.AB[0], (R)bra.AB[1], (R)bra.AB[2]};
       R CD[3] = {(R)ket.AB[0], (R)ket.AB[1], (R)ket.AB[2]};
       C::template hrr<R>(acc, I, AB, CD);

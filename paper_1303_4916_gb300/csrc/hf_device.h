@@ -195,3 +195,6 @@ void hf_register_classes_d5(EriClassOps* table);
 void hf_register_classes_d6(EriClassOps* table);
 // Rys route: every class's jkrys, and all kernels of the f/g classes
 void hf_register_classes_rys(EriClassOps* table);
+// (rys_thread.cu) thread-per-quartet launchers of the small f/g classes,
+// null for the others
+void hf_rys_thread_classes(jk_launch_fn* jk, occ_fn* occ);

@@ -1114,6 +1114,9 @@ void register_all(EriClassOps* table, std::index_sequence<I...>) {
   const store_launch_fn store[] = {&store_launch<(int)I>...};
   const schwarz_launch_fn schw[] = {&schwarz_launch<(int)I>...};
   const grad_launch_fn grd[] = {&grad_launch<(int)I>...};
+  jk_launch_fn jkt[HF_NCLASS] = {};
+  occ_fn occt[HF_NCLASS] = {};
+  ::hf_rys_thread_classes(jkt, occt);
   for (int c = 0; c < HF_NCLASS; ++c) {
     EriClassOps& e = table[c];
     e.jkrys = jk[c];
@@ -1130,6 +1133,11 @@ void register_all(EriClassOps* table, std::index_sequence<I...>) {
     e.store = store[c];
     e.schwarz = schw[c];
     e.chunk = 1;
+    if (jkt[c]) {  // small f/g class: 32 kets per item, one per lane
+      e.jk64 = e.jk32 = e.jkdf = jkt[c];
+      e.occ64 = e.occ32 = e.occdf = occt[c];
+      e.chunk = 32;
+    }
     // operation count per primitive quartet (an FMA counts 2): set-up, the
     // rule (two Clenshaw sums per root), then per root the G recurrences,
     // both transfers and the Ix Iy Iz products into the block; per
