@@ -536,7 +536,7 @@ def run_ours(args):
         except Exception as e:
             extras["serving"] = {"error": f"{type(e).__name__}: {e}"}
         try:
-            extras["rys_water_qz"] = rys_water_qz()
+            extras["rys_water_qz"] = rys_water_qz(cluster=4)
         except Exception as e:
             extras["rys_water_qz"] = {"error": f"{type(e).__name__}: {e}"}
         try:
@@ -691,8 +691,8 @@ def measure_c3(budget_s=900.0, modes=("fp32_split_df64", "df64", "fp64")):
     opts = {"fp64": hf.jk_opts(schwarz_tau=1e-12),
             "df64": hf.jk_opts(schwarz_tau=1e-12, df64=True),
             "fp32_split_df64": hf.jk_opts(schwarz_tau=1e-12, fp32_bound=1e-5, df64=True)}
-    # relative cost of a mode, from measured 40-atom ratios (fp64 : df64 : split+df64 = 4.5 : 1.1 : 1)
-    rel = {"fp32_split_df64": 1.0, "df64": 1.1, "fp64": 4.5}
+    # relative cost of a mode, measured on this molecule (fp64 411 s, df64 173 s, split+df64 143 s)
+    rel = {"fp32_split_df64": 1.0, "df64": 1.2, "fp64": 2.9}
     stream = torch.cuda.current_stream()
     out, res, skipped = {}, {}, {}
     first_s = None
