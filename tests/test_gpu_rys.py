@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from synth import lattice_molecule, random_shells_molecule, water_qz
+from synth import lattice_molecule, random_shells_molecule, small_f_molecule, water_qz
 
 pytestmark = pytest.mark.gpu
 
@@ -183,3 +183,26 @@ def test_batch_with_fg_molecule_matches_single(ctx, hf):
     assert status == [0, 0]
     for s, b in zip(single, batch):
         assert abs(s.energy - b.energy) <= 1e-9
+
+
+def test_uhf_jk_fg_matches_oracle(ctx, hf):
+    """One integral evaluation feeding J[Da + Db], K[Da] and K[Db] through the
+    Rys kernels (warp and thread forms) against the oracle."""
+    mol = random_shells_molecule((4, 3, 1, 0, 2), 71, nprim=(1, 2), exp_range=(0.2, 5.0), box=3.5)
+    ob = oracle.Basis(mol)
+    Da, Db = _density(ob.nbf, 1), _density(ob.nbf, 2)
+    J0, _, _ = ob.jk(Da + Db, tau=0.0, nthreads=oracle.oracle_threads())
+    _, Ka0, _ = ob.jk(Da, tau=0.0, nthreads=oracle.oracle_threads())
+    _, Kb0, _ = ob.jk(Db, tau=0.0, nthreads=oracle.oracle_threads())
+    J, Ka, Kb = hf.Basis(ctx, mol).fock_jk_uhf(_t(Da), _t(Db), opts=hf.jk_opts(schwarz_tau=0.0))
+    assert np.abs(J.cpu().numpy() - J0).max() <= JK_TOL
+    assert np.abs(Ka.cpu().numpy() - Ka0).max() <= JK_TOL
+    assert np.abs(Kb.cpu().numpy() - Kb0).max() <= JK_TOL
+
+
+def test_uhf_with_f_shells_matches_oracle(ctx, hf):
+    mol = small_f_molecule(0)   # 8 electrons: a triplet, 5 alpha and 3 beta
+    ro = oracle.uhf(mol, 5, 3, max_iter=200, e_tol=1e-10, diis_size=8, tau=0.0)
+    r = hf.Basis(ctx, mol).uhf(5, 3, max_iter=200, e_tol=1e-10, diis_size=8, schwarz_tau=0.0)
+    assert r.converged and ro.converged
+    assert abs(r.energy - ro.energy) <= E_TOL
