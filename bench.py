@@ -554,6 +554,13 @@ def run_ours(args):
         "config": dict(workload_desc(n), parallelism=("replicas" if world > 1 else "single-gpu")),
         "eri_quartets_per_s": value * nq_total,
         "quartets_per_build": nq_total,
+        # beside the quartet rate: unique Cartesian integrals and primitive
+        # quartets per second, and the counted FP64 work of a whole build
+        "cartesian_integrals_per_s": value * sum(
+            (s_.quartets_fp64 + s_.quartets_fp32) * ((s_.la + 1) * (s_.la + 2) // 2) * ((s_.lb + 1) * (s_.lb + 2) // 2)
+            * ((s_.lc + 1) * (s_.lc + 2) // 2) * ((s_.ld + 1) * (s_.ld + 2) // 2) for s_ in stats),
+        "prim_quartets_per_s": value * sum(s_.prim_quartets_fp64 + s_.prim_quartets_fp32 for s_ in stats),
+        "build_tflops_fp64": all_flops * value / 1e12,
         "scf": {"latency_s": scf_latency, "iterations": scf.iterations, "converged": scf.converged,
                 "energy": scf.energy, "fock_builds": scf.fock_builds},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
