@@ -10,6 +10,7 @@ from .molecules import (  # noqa: F401
     water_qz,
     water_cluster_qz,
     small_f_molecule,
+    small_g_molecule,
     Molecule,
     h_line,
     lattice_molecule,

@@ -253,6 +253,18 @@ def small_f_molecule(seed: int = 0) -> Molecule:
     return _pack([8, 1], xyz, shells, f"small_f_s{seed}", seed)
 
 
+def small_g_molecule(seed: int = 0) -> Molecule:
+    """O-H (1.9 bohr) with a g shell on O and a d shell on H: O s(3) s(1)
+    p(2) g(1), H s(2) d(1) (primitives in parentheses), exponents
+    log-uniform in [0.3, 6], coefficients uniform in [0.2, 1]; 8 electrons
+    (the cation)."""
+    rng = np.random.default_rng(seed)
+    xyz = np.array([[0.0, 0.0, 0.0], [0.2, 0.1, 1.9]])
+    spec = [(0, 0, 3), (0, 0, 1), (0, 1, 2), (0, 4, 1), (1, 0, 2), (1, 2, 1)]
+    shells = [(a, l, _log_uniform(rng, 0.3, 6.0, k), rng.uniform(0.2, 1.0, size=k)) for a, l, k in spec]
+    return _pack([8, 1], xyz, shells, f"small_g_s{seed}", seed)
+
+
 def random_shells_molecule(ls, seed: int, nprim=(1, 3), exp_range=(0.2, 3.0),
                            box: float = 1.5, coef_range=(0.2, 1.0),
                            Z=None) -> Molecule:

@@ -3,7 +3,7 @@
 differences of its converged energy at steps 2e-3 and 1e-3 bohr, Richardson
 extrapolated; oracle.rhf_gradient) for the molecules the GPU force tests
 use: a 2-atom H chain (s), a 3-atom s+p lattice molecule, a 3-atom s+p+d
-lattice molecule and an O-H pair with an f shell.
+lattice molecule, an O-H pair with an f shell and one with a g shell.
 
 Calls only the CPU oracle (oracle/) and the seeded input generators
 (synth/).  Usage: python tests/golden/make_gradients.py
@@ -17,13 +17,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 import oracle  # noqa: E402
-from synth import h_line, lattice_molecule, small_f_molecule  # noqa: E402
+from synth import h_line, lattice_molecule, small_f_molecule, small_g_molecule  # noqa: E402
 
 CASES = {
     "h_line2": lambda: h_line(2, seed=0),
     "lattice3_sp": lambda: lattice_molecule(3, 1, "sp"),
     "lattice3_spd": lambda: lattice_molecule(3, 3, "spd"),
     "small_f": lambda: small_f_molecule(0),
+    "small_g": lambda: small_g_molecule(0),
 }
 
 

@@ -14,7 +14,7 @@ import os
 import numpy as np
 import pytest
 
-from synth import h_line, lattice_molecule, small_f_molecule
+from synth import h_line, lattice_molecule, small_f_molecule, small_g_molecule
 
 pytestmark = pytest.mark.gpu
 
@@ -25,6 +25,7 @@ MOLS = {
     "lattice3_sp": lambda: lattice_molecule(3, 1, "sp"),
     "lattice3_spd": lambda: lattice_molecule(3, 3, "spd"),
     "small_f": lambda: small_f_molecule(0),
+    "small_g": lambda: small_g_molecule(0),
 }
 
 

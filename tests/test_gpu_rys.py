@@ -59,6 +59,15 @@ FG_CASES = [((3,), 1, (1, 3)), ((3, 0), 2, (1, 3)), ((3, 1, 0), 3, (1, 3)), ((4,
             ((3, 3, 2), 9, (1, 2))]
 
 
+def test_eri_tensor_fg_far_apart(ctx, hf):
+    """Centres ~10 bohr apart with tight exponents: T = pq/(p+q) |PQ|^2 well
+    above 60, where the rule takes its Gauss-Hermite limit."""
+    mol = random_shells_molecule((3, 2, 4), 10, nprim=(1, 2), exp_range=(2.0, 8.0), box=14.0)
+    G0 = oracle.Basis(mol).eri_tensor()
+    G = hf.Basis(ctx, mol).eri_tensor().cpu().numpy()
+    assert np.abs(G - G0).max() <= ERI_TOL
+
+
 @pytest.mark.parametrize("ls,seed,nprim", FG_CASES)
 def test_eri_tensor_fg_classes(ctx, hf, ls, seed, nprim):
     mol = random_shells_molecule(ls, seed, nprim=nprim, exp_range=(0.2, 6.0), box=2.5)
