@@ -540,6 +540,10 @@ def run_ours(args):
         except Exception as e:
             extras["rys_water_qz"] = {"error": f"{type(e).__name__}: {e}"}
         try:
+            extras["mp2_40_atom"] = measure_mp2(mol)
+        except Exception as e:
+            extras["mp2_40_atom"] = {"error": f"{type(e).__name__}: {e}"}
+        try:
             left = args.extras_budget - (time.perf_counter() - t_ex)
             extras["c3_150_atom"] = measure_c3(budget_s=max(0.0, left), modes=("fp32_split_df64", "fp64"))
         except Exception as e:
@@ -1055,6 +1059,30 @@ def rys_water_qz(steps=10, warmup=3, cluster=8):
     basis.close()
     if cluster > 0:
         out["cluster"] = rys_cluster(ctx, cluster, steps=max(2, steps // 3))
+    return out
+
+
+def measure_mp2(mol):
+    """MP2 correlation energy of the converged RHF state of mol: the AO
+    tensor (nbf^4 doubles) built and held in HBM, four one-index transforms
+    (cuBLAS DGEMM) and the energy sum; wall time of hf_mp2_energy."""
+    import torch
+    import paper_1303_4916_gb300 as hf
+    ctx = hf.Context(0)
+    basis = hf.Basis(ctx, mol)
+    r = basis.scf(max_iter=128, e_tol=1e-10, diis_size=8)
+    no = mol.n_electrons // 2
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2 = basis.mp2_energy(r.tensors["C"], r.tensors["eps"], no)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    n = basis.nbf
+    out = {"workload": f"{mol.natom}-atom s+p molecule, nbf {n}, n_occ {no}", "e_mp2": e2, "seconds": dt,
+           "ao_tensor_gb": n ** 4 * 8 / 1e9,
+           "transform_tflops_fp64": 2.0 * (n ** 4 * no + n ** 3 * no * (n - no) + n ** 2 * no * no * (n - no)
+                                           + n * no * no * (n - no) ** 2) / dt / 1e12}
+    basis.close()
     return out
 
 

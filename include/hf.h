@@ -64,6 +64,8 @@ extern "C" {
                                       g shell take the Rys-quadrature route (Eq. 5 by Rys
                                       quadrature, as the paper evaluates it) */
 #define HF_MAX_NPRIM 16            /* most primitives in one contracted shell */
+#define HF_STORED_NBF_MAX 400      /* largest nbf of the stored-tensor calls (nbf^4 doubles:
+                                      205 GB at 400, held in HBM) */
 
 /* ---------------------------------------------------------------- types */
 
@@ -113,7 +115,8 @@ typedef struct {
 } hf_jk_opts;
 
 /* SCF options.  hf_scf_opts_default() fills the defaults shown. */
-#define HF_SCF_STORED_ERI 1u       /* build the N^4 ERI tensor once and contract it (small N only) */
+#define HF_SCF_STORED_ERI 1u       /* build the N^4 ERI tensor once and contract it
+                                      (nbf <= HF_STORED_NBF_MAX, device memory permitting) */
 typedef struct {
     int max_iter;        /* default 128 */
     double e_tol;        /* stop when |E_k - E_{k-1}| <= e_tol (default 1e-8) */
@@ -273,7 +276,8 @@ int hf_fock_jk_noalloc(hf_basis* b, const double* D, double* J, double* K, const
 int hf_one_electron(hf_basis* b, double* S, double* T, double* V, double* e_nuc);
 
 /* Full ERI tensor G[i][j][k][l] = (ij|kl) of Eq. 5 into a DEVICE buffer of
- * nbf^4 doubles (small bases only: nbf <= 128).  Errors: HF_ERR_INVALID. */
+ * nbf^4 doubles (nbf <= HF_STORED_NBF_MAX; the caller allocates it).
+ * Errors: HF_ERR_INVALID. */
 int hf_eri_tensor(hf_basis* b, double* G);
 
 /* J and K from a stored ERI tensor G (device, nbf^4): J = G vec(D),
@@ -345,8 +349,10 @@ int hf_uhf_solve(hf_basis* b, int n_alpha, int n_beta, const hf_scf_opts* opts, 
  *   E(2) = sum_{i,j occ} sum_{a,b virt} (ia|jb) [2 (ia|jb) - (ib|ja)]
  *                                        / (e_i + e_j - e_a - e_b)
  * over the canonical orbitals, (ia|jb) from the stored AO tensor of Eq. 5
- * by four one-index transformations (small bases: nbf <= 128; the call
- * allocates nbf^4 + nbf^3 n_occ doubles of device memory while it runs).
+ * by four one-index transformations (nbf <= HF_STORED_NBF_MAX; the call
+ * allocates nbf^4 + nbf^3 n_occ + nbf^2 n_occ n_virt doubles of device memory
+ * while it runs, 30 GB at nbf 220, and returns HF_ERR_OOM when they do not
+ * fit).
  * C: nbf x nbf DEVICE, row-major, C[mu][p] = coefficient of AO mu in MO p
  * (as hf_scf_result.C); eps: nbf orbital energies, ascending, DEVICE;
  * n_occ in [1, nbf).  *e2 (host) receives E(2).  Errors: HF_ERR_INVALID,

@@ -29,6 +29,7 @@ HF_ERR_CANCELLED = -11
 HF_ERR_TOO_LARGE = -12
 HF_LMAX = 4
 HF_MAX_NPRIM = 16
+HF_STORED_NBF_MAX = 400
 
 HF_JK_HOST = 1
 HF_JK_DETERMINISTIC = 2

@@ -833,7 +833,8 @@ extern "C" int hf_fock_jk_uhf(hf_basis* b, const double* Da, const double* Db, d
 // ------------------------------------------------------------- ERI tensor
 extern "C" int hf_eri_tensor(hf_basis* b, double* G) {
   if (!b || !G) return hf_fail(HF_ERR_INVALID, "hf_eri_tensor: null argument");
-  if (b->nbf > 128) return hf_fail(HF_ERR_INVALID, "hf_eri_tensor: nbf %d above 128", b->nbf);
+  if (b->nbf > HF_STORED_NBF_MAX)
+    return hf_fail(HF_ERR_INVALID, "hf_eri_tensor: nbf %d above %d", b->nbf, HF_STORED_NBF_MAX);
   hf_ctx* ctx = b->ctx;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
@@ -890,7 +891,8 @@ int hf_jk_stored_device(hf_basis* b, const double* G, const double* D, double* J
 
 extern "C" int hf_jk_stored(hf_basis* b, const double* G, const double* D, double* J, double* K) {
   if (!b || !G || !D || !J || !K) return hf_fail(HF_ERR_INVALID, "hf_jk_stored: null argument");
-  if (b->nbf > 128) return hf_fail(HF_ERR_INVALID, "hf_jk_stored: nbf %d above 128", b->nbf);
+  if (b->nbf > HF_STORED_NBF_MAX)
+    return hf_fail(HF_ERR_INVALID, "hf_jk_stored: nbf %d above %d", b->nbf, HF_STORED_NBF_MAX);
   hf_ctx* ctx = b->ctx;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);

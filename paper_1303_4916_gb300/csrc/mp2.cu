@@ -1,5 +1,6 @@
 // mp2.cu -- second-order Moller-Plesset correlation energy of a closed-shell
-// RHF solution (the paper's MP2 follows Szabo-Ostlund), small-basis form.
+// RHF solution (the paper's MP2 follows Szabo-Ostlund), from the AO tensor
+// held in HBM (nbf <= HF_STORED_NBF_MAX).
 //
 //   E(2) = sum_{i,j occ} sum_{a,b virt} (ia|jb) [2 (ia|jb) - (ib|ja)]
 //                                        / (e_i + e_j - e_a - e_b)
@@ -63,7 +64,8 @@ int transform(hf_ctx* ctx, const double* in, long long L, const double* M, int T
 extern "C" int hf_mp2_energy(hf_basis* b, const double* C, const double* eps, int n_occ, double* e2) {
   if (!b || !C || !eps || !e2) return hf_fail(HF_ERR_INVALID, "hf_mp2_energy: null argument");
   const int n = b->nbf;
-  if (n > 128) return hf_fail(HF_ERR_INVALID, "hf_mp2_energy: nbf %d above 128 (stored AO tensor)", n);
+  if (n > HF_STORED_NBF_MAX)
+    return hf_fail(HF_ERR_INVALID, "hf_mp2_energy: nbf %d above %d (stored AO tensor)", n, HF_STORED_NBF_MAX);
   if (n_occ < 1 || n_occ >= n) return hf_fail(HF_ERR_INVALID, "hf_mp2_energy: n_occ %d outside [1, nbf)", n_occ);
   hf_ctx* ctx = b->ctx;
   std::lock_guard<std::mutex> lk(ctx->mu);

@@ -474,7 +474,7 @@ extern "C" int hf_scf_solve(hf_basis* b, const hf_scf_opts* opts, hf_scf_result*
   HF_CHECK(scf_state_init(b, s, o.diis_size));
   DevArray<double> G;
   if (o.flags & HF_SCF_STORED_ERI) {
-    if (b->nbf > 128) return hf_fail(HF_ERR_INVALID, "stored ERI needs nbf <= 128");
+    if (b->nbf > HF_STORED_NBF_MAX) return hf_fail(HF_ERR_INVALID, "stored ERI needs nbf <= %d", HF_STORED_NBF_MAX);
     HF_CHECK(G.alloc(ctx, (size_t)b->nbf * b->nbf * b->nbf * b->nbf));
     HF_CHECK(hf_eri_tensor_device(b, G.ptr));
   }

@@ -2,6 +2,9 @@
 closed-shell formula over canonical orbitals) against the oracle's mp2:
 with the oracle's own orbitals as input (the transform and the sum alone),
 and end to end from the GPU's RHF."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -64,3 +67,21 @@ def test_mp2_rejects_bad_arguments(ctx, hf):
         with pytest.raises(hf.HFError) as e:
             basis.mp2_energy(C, eps, no)
         assert e.value.code == _abi.HF_ERR_INVALID
+
+
+def test_mp2_and_stored_eri_beyond_128_functions(ctx, hf):
+    """nbf 140 (28 nuclei with one f, d, p or s shell each, so the Rys
+    classes too): the AO tensor (3.1 GB) held in HBM for the MP2 transform
+    and for the stored-ERI SCF, against the oracle's energies
+    (tests/golden/make_mp2_large.py)."""
+    from synth import random_shells_molecule
+    ref = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mp2_large.json")))
+    mol = random_shells_molecule([3, 2, 1, 0] * 7, 4, nprim=(1, 1), exp_range=(0.3, 3.0), box=10.0)
+    basis = hf.Basis(ctx, mol)
+    assert basis.nbf == ref["nbf"] > 128
+    r = basis.scf(max_iter=128, e_tol=1e-11, diis_size=8, schwarz_tau=0.0)
+    assert r.converged and abs(r.energy - ref["energy"]) <= 1e-8
+    e2 = basis.mp2_energy(r.tensors["C"], r.tensors["eps"], mol.n_electrons // 2)
+    assert abs(e2 - ref["e_mp2"]) <= 1e-8, (e2, ref["e_mp2"])
+    rs = basis.scf(max_iter=128, e_tol=1e-11, diis_size=8, schwarz_tau=0.0, stored_eri=True, outputs=False)
+    assert rs.converged and abs(rs.energy - ref["energy"]) <= 1e-8
