@@ -24,8 +24,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["rys_thread.cu", "eri_d6.cu", "eri_d5.cu", "eri_d4.cu", "eri_d3.cu", "eri_d2.cu", "eri_d1.cu", "eri_sp.cu",
            "rys.cu", "grad.cu", "api.cu", "basis.cu", "onee.cu", "scf.cu", "batch.cu", "serve.cu", "noalloc.cu", "multi.cu",
            "mp2.cu"]
-KERNEL_HEADERS = ["eri.cuh", "eri_classes.cuh", "hf_device.h"]
-HEADERS = KERNEL_HEADERS + ["rys.cuh", "hf_internal.h", "scf_internal.h", "multi.h", "../../include/hf.h"]
+KERNEL_HEADERS = ["eri.cuh", "eri_classes.cuh", "hf_device.h", "rys.cuh", "df64.cuh"]
+HEADERS = KERNEL_HEADERS + ["hf_internal.h", "scf_internal.h", "multi.h", "../../include/hf.h"]
 LMAX = 2
 
 

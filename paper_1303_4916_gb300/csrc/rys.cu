@@ -20,11 +20,15 @@
 //                         G(ia + k, ic + l),
 // and (ab|cd) = sum over roots and primitive quartets of Ix Iy Iz.
 //
-// One warp per contracted quartet: the G tables, both transfers and the
-// contracted output block live in the warp's slice of shared memory; the
-// output block is built in chunks of whole a-components (all b, c, d),
-// each chunk over the whole primitive loop, then digested into J and K
-// like the cooperative kernels do (same symmetry weights and accumulators).
+// One warp per work item: a chunk of one contracted quartet's output block
+// (whole (a, b) rows, all c, d, at most 1024 outputs) over a range of its
+// primitive quartets.  The G tables and both transfers live in the warp's
+// slice of shared memory; each lane keeps up to 32 of the chunk's outputs
+// in registers; the finished chunk is digested into J and K as the
+// cooperative kernels do (same symmetry weights and accumulators).  The
+// smallest f/g classes run one quartet per lane instead (rys_thread.cu).
+// The gradient's derivative kernel (rys_grad_kernel) shares the tables,
+// one power higher on A, B and C.
 #include <algorithm>
 #include <array>
 #include <cfloat>

@@ -1,8 +1,7 @@
-// rys.cuh -- Rys quadrature for the electron repulsion integrals of Eq. 5
-// (the paper evaluates them by Rys quadrature): roots and weights of the
-// Rys rule, and the warp-per-shell-quartet kernels of the Rys route that
-// serve every shell quartet with an f or g shell (and, on request, all
-// classes).
+// rys.cuh -- the Rys quadrature rule behind the electron repulsion
+// integrals of Eq. 5 (the paper evaluates them by Rys quadrature): the
+// layout of the table of roots and weights, and its evaluation, shared by
+// the device kernels (rys.cu, eri.cuh, onee.cu, grad.cu) and the host.
 //
 // The n-point Rys rule for a primitive quartet with T = rho |PQ|^2 is the
 // Gauss rule of the weight exp(-T t^2) on t in [0, 1] in the variable
@@ -14,8 +13,8 @@
 // n = floor(L/2) + 1 roots make it exact.
 //
 // Table: for n = 1..RYS_NMAX and T in [0, RYS_TMAX), intervals of width
-// RYS_H; per interval and root a Chebyshev series of RYS_NCHEB terms for
-// u_i(T) and one for w_i(T) in x = 2 (T - T_j) / RYS_H - 1.  For
+// 1 / RYS_INV_H; per interval and root a Chebyshev series of RYS_NCHEB
+// terms for u_i(T) and one for w_i(T) in x = 2 RYS_INV_H (T - T_j) - 1.  For
 // T >= RYS_TMAX the half-range Gauss-Hermite limit is used:
 // u_i = s_i^2 / T and w_i = W_i / sqrt(T), with s_i > 0 the positive nodes
 // and W_i the weights of the 2n-point Gauss-Hermite rule (the integral to
@@ -30,7 +29,6 @@
 #define RYS_NINT 120
 #define RYS_INV_H 2.0    // 1 / interval width
 #define RYS_TMAX 60.0
-#define RYS_LMAX_SHELL 4  // highest shell l of the route
 
 // offset of the n-point block: n (n - 1) / 2 earlier roots per interval
 __host__ __device__ constexpr int rys_tab_off(int n) { return RYS_NINT * 2 * RYS_NCHEB * ((n - 1) * n / 2); }
